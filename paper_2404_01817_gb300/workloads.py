@@ -1,0 +1,314 @@
+"""Seeded synthetic inputs for population-wide NEAT genome evaluation.
+
+This module only *draws* inputs: genome tensors in the paper's NaN-padded
+encoding (Section 3.1, "Tensorized Encodings") and observation batches.  It
+holds none of the evaluation arithmetic (no topological sort, no forward pass,
+no activation or aggregation function).  Both the CUDA path and the oracle are
+fed from here; neither imports the other.
+
+Genome encoding (Section 3.1):
+  nodes f32[P][Nmax][5]  row = (key, bias, response, aggregation id, activation id)
+  conns f32[P][Cmax][4]  row = (in key, out key, enabled, weight)
+Absent rows are all-NaN.  Input nodes carry keys 0..I-1, output nodes keys
+I..I+O-1 (the genome interface's ``input_idx``/``output_idx``, Appendix
+"Interfaces", Listing 2), hidden nodes keys from I+O upward.
+
+Categorical ids are stored as floats (Section 3.1 gives tanh = 1, sigmoid = 2;
+the rest of the table is this library's reading):
+  activation: 0 identity, 1 tanh, 2 sigmoid, 3 relu, 4 sin, 5 gauss, 6 abs
+  aggregation: 0 sum, 1 product, 2 max, 3 mean
+
+Workload recipes follow the experiment settings of Appendix "Experiment
+Detail" (weights and biases N(0,1), response 1, tanh, sum) widened to the five
+evaluation shapes this library is measured on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Callable, Sequence
+
+import numpy as np
+
+ACT_IDENTITY, ACT_TANH, ACT_SIGMOID, ACT_RELU, ACT_SIN, ACT_GAUSS, ACT_ABS = range(7)
+AGG_SUM, AGG_PRODUCT, AGG_MAX, AGG_MEAN = range(4)
+ALL_ACTS = tuple(range(7))
+ALL_AGGS = tuple(range(4))
+
+NODE_COLS = 5
+CONN_COLS = 4
+
+
+def rng_for(seed: int, *stream: int) -> np.random.Generator:
+    """PCG64 generator for (seed, stream...) — independent substreams."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, *stream])))
+
+
+@dataclass
+class Population:
+    """A population in the padded encoding plus its shape parameters."""
+    nodes: np.ndarray          # f32 [P][Nmax][5]
+    conns: np.ndarray          # f32 [P][Cmax][4]
+    num_inputs: int
+    num_outputs: int
+
+    @property
+    def pop(self) -> int:
+        return self.nodes.shape[0]
+
+    @property
+    def max_nodes(self) -> int:
+        return self.nodes.shape[1]
+
+    @property
+    def max_conns(self) -> int:
+        return self.conns.shape[1]
+
+    def subset(self, idx) -> "Population":
+        idx = np.asarray(idx)
+        return Population(np.ascontiguousarray(self.nodes[idx]),
+                          np.ascontiguousarray(self.conns[idx]),
+                          self.num_inputs, self.num_outputs)
+
+
+def empty_population(pop: int, max_nodes: int, max_conns: int,
+                     num_inputs: int, num_outputs: int) -> Population:
+    nodes = np.full((pop, max_nodes, NODE_COLS), np.nan, dtype=np.float32)
+    conns = np.full((pop, max_conns, CONN_COLS), np.nan, dtype=np.float32)
+    return Population(nodes, conns, num_inputs, num_outputs)
+
+
+def _sample_pairs(rng: np.random.Generator, n_in: int, n_non_input: int,
+                  n_edges: int) -> np.ndarray:
+    """Draw ``n_edges`` distinct (src, dst) pairs of a random DAG.
+
+    Non-input nodes are indexed by a rank 0..m-1 (all inputs rank below every
+    non-input).  A pair is any src of lower rank than its non-input dst.  Pairs
+    are drawn uniformly without replacement by index into the concatenation of
+    per-dst source lists.  Returns int64 [n_edges, 2] of (src, dst) where a
+    value < n_in is input number v and v >= n_in is non-input rank v - n_in.
+    """
+    m = n_non_input
+    counts = n_in + np.arange(m, dtype=np.int64)          # sources of rank r
+    total = int(counts.sum())
+    n_edges = min(n_edges, total)
+    if n_edges <= 0:
+        return np.zeros((0, 2), dtype=np.int64)
+    cum = np.concatenate([[0], np.cumsum(counts)])
+    if n_edges * 3 > total:
+        picks = rng.choice(total, size=n_edges, replace=False)
+    else:
+        picks = np.zeros(0, dtype=np.int64)
+        while picks.size < n_edges:
+            extra = rng.integers(0, total, size=2 * (n_edges - picks.size) + 8)
+            picks = np.unique(np.concatenate([picks, extra]))
+        picks = rng.permutation(picks)[:n_edges]
+    dst_rank = np.searchsorted(cum, picks, side="right") - 1
+    s = picks - cum[dst_rank]
+    src = np.where(s < n_in, s, n_in + (s - n_in))            # same numbering
+    dst = n_in + dst_rank
+    return np.stack([src, dst], axis=1)
+
+
+def random_dag_population(seed: int, pop: int, num_inputs: int, num_outputs: int,
+                          max_nodes: int, max_conns: int,
+                          hidden: Callable[[np.random.Generator], int],
+                          edges: Callable[[np.random.Generator, int], int],
+                          acts: Sequence[int] = (ACT_TANH,),
+                          aggs: Sequence[int] = (AGG_SUM,),
+                          p_disabled: float = 0.1,
+                          response: Callable[[np.random.Generator, int], np.ndarray] | None = None,
+                          stream: int = 0) -> Population:
+    """Random feedforward genomes in the canonical row layout.
+
+    Per genome: H = hidden(rng) hidden nodes (clamped to capacity); the O + H
+    non-input nodes get a random rank; E = edges(rng, n) connections are drawn
+    without duplicates among pairs (lower rank -> higher rank, dst non-input);
+    each connection is disabled with probability ``p_disabled``; connection
+    rows are shuffled.  Weights and biases N(0,1); response 1 unless a sampler
+    is given; activation/aggregation ids uniform over ``acts``/``aggs``.
+    """
+    I, O = num_inputs, num_outputs
+    P = empty_population(pop, max_nodes, max_conns, I, O)
+    acts = np.asarray(acts, dtype=np.float32)
+    aggs = np.asarray(aggs, dtype=np.float32)
+    for g in range(pop):
+        rng = rng_for(seed, stream, g)
+        H = int(min(max(hidden(rng), 0), max_nodes - I - O))
+        n = I + O + H
+        m = O + H
+        keys = np.arange(n, dtype=np.float32)                 # row r holds key r
+        nodes = P.nodes[g]
+        nodes[:n, 0] = keys
+        nodes[:n, 1] = rng.standard_normal(n).astype(np.float32)
+        nodes[:n, 2] = (response(rng, n).astype(np.float32) if response is not None
+                        else np.float32(1.0))
+        nodes[:n, 3] = aggs[rng.integers(0, aggs.size, size=n)]
+        nodes[:n, 4] = acts[rng.integers(0, acts.size, size=n)]
+        # non-input rank -> node row: a random permutation of rows I..n-1
+        rank_row = I + rng.permutation(m)
+        E = int(min(edges(rng, n), max_conns))
+        pairs = _sample_pairs(rng, I, m, E)
+        E = pairs.shape[0]
+
+        def to_row(v):
+            return np.where(v < I, v, rank_row[np.clip(v - I, 0, m - 1)])
+
+        src_row = to_row(pairs[:, 0])
+        dst_row = to_row(pairs[:, 1])
+        conns = P.conns[g]
+        conns[:E, 0] = keys[src_row]
+        conns[:E, 1] = keys[dst_row]
+        conns[:E, 2] = (rng.random(E) >= p_disabled).astype(np.float32)
+        conns[:E, 3] = rng.standard_normal(E).astype(np.float32)
+    return P
+
+
+# --------------------------------------------------------------------------
+# The five evaluation shapes
+# --------------------------------------------------------------------------
+
+def xor_population(seed: int = 0, pop: int = 100, mutations: int = 5) -> Population:
+    """XOR-shaped genomes grown by NEAT-style structural mutations.
+
+    2 inputs + 1 bias input (key 2, fed 1.0), 1 output (key 3), start fully
+    connected (3 conns), then ``mutations`` mutations, each add-node or
+    add-conn with probability 1/2 (Section 3.2's row insertions):
+      add-node: pick a random enabled conn a->b, disable it, add node c with
+                conns a->c and c->b (weights N(0,1)), bias N(0,1);
+      add-conn: pick uniformly among absent pairs a->b (b not an input) that
+                keep the graph acyclic, using a maintained linear extension;
+                no-op when none is left.
+    Max 10 nodes / 20 conns, sigmoid, sum, response 1.
+    """
+    I, O, NMAX, CMAX = 3, 1, 10, 20
+    P = empty_population(pop, NMAX, CMAX, I, O)
+    for g in range(pop):
+        rng = rng_for(seed, 1, g)
+        node_keys = [0, 1, 2, 3]
+        bias = {k: float(rng.standard_normal()) for k in node_keys}
+        conns = [[k, 3, 1.0, float(rng.standard_normal())] for k in (0, 1, 2)]
+        linear = [0, 1, 2, 3]              # inputs first; every edge goes forward in it
+        next_key = 4
+        for _ in range(mutations):
+            if rng.random() < 0.5:
+                enabled = [i for i, c in enumerate(conns) if c[2] != 0.0]
+                if not enabled or len(node_keys) >= NMAX or len(conns) + 2 > CMAX:
+                    continue
+                ci = enabled[int(rng.integers(len(enabled)))]
+                a, b = conns[ci][0], conns[ci][1]
+                conns[ci][2] = 0.0
+                c = next_key
+                next_key += 1
+                node_keys.append(c)
+                bias[c] = float(rng.standard_normal())
+                linear.insert(linear.index(b), c)
+                conns.append([a, c, 1.0, float(rng.standard_normal())])
+                conns.append([c, b, 1.0, float(rng.standard_normal())])
+            else:
+                if len(conns) >= CMAX:
+                    continue
+                present = {(c[0], c[1]) for c in conns}
+                cand = [(a, b) for ia, a in enumerate(linear) for b in linear[ia + 1:]
+                        if b >= I and (a, b) not in present]
+                if not cand:
+                    continue
+                a, b = cand[int(rng.integers(len(cand)))]
+                conns.append([a, b, 1.0, float(rng.standard_normal())])
+        nd = P.nodes[g]
+        for r, k in enumerate(node_keys):
+            nd[r] = (k, bias[k], 1.0, AGG_SUM, ACT_SIGMOID)
+        P.conns[g, :len(conns)] = np.asarray(conns, dtype=np.float32)
+    return P
+
+
+def xor_inputs(pop: int = 100) -> np.ndarray:
+    """The 4 points of {0,1}^2 with the constant bias input: f32 [P][4][3]."""
+    pts = np.array([[0, 0, 1], [0, 1, 1], [1, 0, 1], [1, 1, 1]], dtype=np.float32)
+    return np.ascontiguousarray(np.broadcast_to(pts, (pop, 4, 3)))
+
+
+def ant_population(seed: int = 0, pop: int = 10000) -> Population:
+    """Ant-shaped control genomes: 27 inputs, 8 outputs, max 50 nodes / 200 conns.
+
+    Hidden count uniform on 0..15: the stated 0..20 cannot fit, since
+    27 + 8 + 20 > 50 rows, so it is clamped to capacity.  100..200 conns drawn
+    (capped by the available acyclic pairs), 10% disabled, tanh, sum.
+    """
+    return random_dag_population(
+        seed, pop, 27, 8, 50, 200,
+        hidden=lambda r: int(r.integers(0, 16)),
+        edges=lambda r, n: int(r.integers(100, 201)),
+        acts=(ACT_TANH,), aggs=(AGG_SUM,), p_disabled=0.1, stream=2)
+
+
+BATCHED_MAX_NODES = (16, 64, 256, 1024)
+
+
+def batched_populations(seed: int = 0, pop: int = 2048,
+                        max_nodes: Sequence[int] = BATCHED_MAX_NODES,
+                        num_inputs: int = 8, num_outputs: int = 4) -> list[Population]:
+    """Uneven populations: one per Nmax, Cmax = 4 Nmax, n ~ U{I+O..Nmax} nodes,
+    E ~ U{3n..4n} conns, 10% disabled, all 7 activations and 4 aggregations
+    drawn uniformly."""
+    out = []
+    for j, nmax in enumerate(max_nodes):
+        I, O = num_inputs, num_outputs
+        out.append(random_dag_population(
+            seed, pop, I, O, nmax, 4 * nmax,
+            hidden=lambda r, nmax=nmax: int(r.integers(0, nmax - I - O + 1)),
+            edges=lambda r, n: int(r.integers(3 * n, 4 * n + 1)),
+            acts=ALL_ACTS, aggs=ALL_AGGS, p_disabled=0.1, stream=10 + j))
+    return out
+
+
+def cppn_population(seed: int = 0, pop: int = 1000) -> Population:
+    """CPPN genomes: inputs (x_s, y_s, x_d, y_d, 1), 1 output, max 32 nodes /
+    96 conns, hidden U{0..26}, E ~ U{5..96}, sin/gauss/tanh/identity, sum."""
+    return random_dag_population(
+        seed, pop, 5, 1, 32, 96,
+        hidden=lambda r: int(r.integers(0, 27)),
+        edges=lambda r, n: int(r.integers(5, 97)),
+        acts=(ACT_SIN, ACT_GAUSS, ACT_TANH, ACT_IDENTITY), aggs=(AGG_SUM,),
+        p_disabled=0.1, stream=3)
+
+
+def normal_inputs(seed: int, shape, stream: int = 0) -> np.ndarray:
+    """N(0,1) float32 observations of the given shape (host memory)."""
+    return rng_for(seed, 100 + stream).standard_normal(shape, dtype=np.float32)
+
+
+def serving_requests(seed: int = 0, n_requests: int = 2000, rate_hz: float = 200.0,
+                     pop_range=(64, 4096), nodes_range=(8, 512), batch_range=(1, 256),
+                     steps: int = 100) -> list[dict]:
+    """Poisson request stream: arrival times and log-uniform shapes.
+
+    Per request: P, Nmax, B log-uniform in their ranges, Cmax = 4 Nmax,
+    I = min(27, Nmax // 2), O = min(8, max(1, Nmax // 4)).  Genomes are drawn
+    lazily with ``request_population``.
+    """
+    rng = rng_for(seed, 5)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_requests))
+
+    def logu(lo, hi):
+        return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+
+    reqs = []
+    for i in range(n_requests):
+        nmax = logu(*nodes_range)
+        reqs.append(dict(id=i, arrival_s=float(t[i]), pop=logu(*pop_range),
+                         max_nodes=nmax, max_conns=4 * nmax,
+                         num_inputs=min(27, nmax // 2),
+                         num_outputs=min(8, max(1, nmax // 4)),
+                         batch=logu(*batch_range), steps=steps, seed=seed * 100003 + i))
+    return reqs
+
+
+def request_population(req: dict) -> Population:
+    """Genomes of one serving request: as the Ant shape, at the request's size."""
+    I, O, nmax = req["num_inputs"], req["num_outputs"], req["max_nodes"]
+    cmax = req["max_conns"]
+    return random_dag_population(
+        req["seed"], req["pop"], I, O, nmax, cmax,
+        hidden=lambda r: int(r.integers(0, max(nmax - I - O, 0) + 1)),
+        edges=lambda r, n: int(r.integers(2 * n, 4 * n + 1)),
+        acts=(ACT_TANH,), aggs=(AGG_SUM,), p_disabled=0.1, stream=6)
