@@ -1,0 +1,372 @@
+"""Benchmark: population-wide NEAT genome evaluation on the Ant-shaped control
+workload (10 000 genomes, 27 inputs, 8 outputs, max 50 nodes / 200 conns,
+tanh, sum; 1000 sequential steps with one N(0,1) observation per genome per
+step).
+
+One bench step = one episode of the hot path: transform the population once,
+then 1000 sequential forwards (Section 3.3: transform once, calculate per
+call).  Two forms are timed on the same data:
+  batched  the 1000 forwards as one CUDA graph with programmatic dependent
+           launch (neat_forward_steps) -- the headline `value`;
+  plain    one neat_forward call per step from the host.
+`e2e` repeats the batched episode through the C ABI with the genome tensors
+and observations in pinned host memory and the actions copied back, all
+inside the timed region.
+
+The episode's observations (1.08 GB) exceed the 129 MB L2, so every episode
+streams its inputs from HBM; the transformed population (~19 MB) stays
+L2-resident across the steps of an episode, as it would between environment
+steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "genome-forwards/s (Ant-shape, 10k pop) batched vs plain, % HBM peak; p50/p99 ms"
+UNIT = "genome-forwards/s"
+POP, I, O, NMAX, CMAX, ENV_STEPS = 10000, 27, 8, 50, 200, 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--env-steps", type=int, default=ENV_STEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(pop, obs_host, seconds_target=15.0):
+    """The FP64 oracle on the host cores over a bounded sample of the workload:
+    all genomes, the first S steps of the episode (S sized from a probe)."""
+    import concurrent.futures as cf
+
+    import oracle
+    cores = os.cpu_count() or 1
+    xs_all = np.ascontiguousarray(obs_host[:, :, 0, :].transpose(1, 0, 2))   # [P][steps][I]
+    t0 = time.perf_counter()
+    oracle.forward(pop.nodes[:200], pop.conns[:200], I, O, xs_all[:200, :50])
+    per_gf = (time.perf_counter() - t0) / (200 * 50)
+    S = int(max(10, min(xs_all.shape[1], seconds_target / max(per_gf, 1e-9) / POP)))
+    chunks = np.array_split(np.arange(POP), cores * 4)
+
+    def run(idx):
+        oracle.forward(pop.nodes[idx], pop.conns[idx], I, O, xs_all[idx, :S])
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(run, chunks))
+    dt = time.perf_counter() - t0
+    return {"value": POP * S / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {POP} genomes x first {S} of the episode's steps (FP64 C oracle, "
+                      f"transform once per genome + forward per step, {cores} threads)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: bounded samples of the same workload."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2404_01817_gb300 import workloads as W
+    pop = W.ant_population(0, POP)
+    obs = W.normal_inputs(0, (60, POP, 1, I))
+    import oracle
+    xs = np.ascontiguousarray(obs[:, :, 0, :].transpose(1, 0, 2))
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 1
+    chunks = np.array_split(np.arange(POP), cores * 4)
+    S = xs.shape[1]
+
+    def episode():
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda idx: oracle.forward(pop.nodes[idx], pop.conns[idx], I, O, xs[idx]), chunks))
+
+    for _ in range(args.warmup):
+        episode()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        episode()
+    dt = time.perf_counter() - t0
+    value = POP * S * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "Ant-shaped control: 10000 genomes, 27 in / 8 out, "
+                                                        "max 50 nodes / 200 conns, tanh, sum",
+                                            "sample": f"{S} steps per bench step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"all {POP} genomes x {S} steps per bench step, FP64 C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+
+    S = args.env_steps
+    pop = W.ant_population(rank, POP)          # each rank evaluates its own population
+    d = neat.dims(I, O, NMAX, CMAX)
+    nodes = torch.from_numpy(pop.nodes).to(dev)
+    conns = torch.from_numpy(pop.conns).to(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + rank)
+    obs = torch.randn((S, POP, 1, I), device=dev, generator=gen)
+    act = torch.empty((S, POP, 1, O), device=dev)
+    rec = torch.empty(neat.neat_transformed_bytes(POP, d), dtype=torch.uint8, device=dev)
+    status = torch.empty(POP, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cache = neat.StepsCache()
+    L_plain = neat.neat_default_launch(d, 1)
+    L_batched = neat.neat_default_launch(d, 1)
+    L_batched.pdl = 1
+
+    def episode_batched():
+        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
+
+    def episode_plain(step_events=None):
+        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        for s in range(S):
+            if step_events is not None:
+                step_events[s][0].record(stream)
+            neat.neat_forward(rec, POP, d, obs[s], act[s], launch=L_plain, stream=stream)
+            if step_events is not None:
+                step_events[s][1].record(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def reduce_max(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up (also builds the CUDA graph)
+    for _ in range(args.warmup):
+        episode_batched()
+    episode_plain()
+    barrier()
+    assert int((status.cpu() & 0xFF).sum()) == 0
+
+    # ---- batched: the headline
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+    fw_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        ev0.record(stream)
+        for k in range(args.steps):
+            ep_events[k][0].record(stream)
+            neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+            fw_events[k][0].record(stream)
+            neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
+            fw_events[k][1].record(stream)
+            ep_events[k][1].record(stream)
+        ev1.record(stream)
+        barrier()
+    t_batched = reduce_max(ev0.elapsed_time(ev1) / 1e3)
+    ep_ms = [a.elapsed_time(b) for a, b in ep_events]
+    fw_ms = [a.elapsed_time(b) for a, b in fw_events]
+    value = world * POP * S * args.steps / t_batched
+
+    # ---- plain: one launch per step from the host, per-step latency
+    n_plain = max(1, min(args.steps, 5))
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(S)]
+    step_ms = []
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(n_plain):
+        episode_plain(step_ev)
+        torch.cuda.synchronize(dev)
+        step_ms += [a.elapsed_time(b) for a, b in step_ev]
+    p1.record(stream)
+    barrier()
+    t_plain = reduce_max(p0.elapsed_time(p1) / 1e3)
+    value_plain = world * POP * S * n_plain / t_plain
+
+    # ---- end to end through the C ABI: host genome tensors + observations in,
+    # actions out, per episode
+    nodes_h = torch.from_numpy(pop.nodes).pin_memory()
+    conns_h = torch.from_numpy(pop.conns).pin_memory()
+    obs_h = obs.cpu().pin_memory()
+    act_h = torch.empty(act.shape, dtype=torch.float32).pin_memory()
+    n_e2e = max(1, min(args.steps, 10))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        nodes.copy_(nodes_h, non_blocking=True)
+        conns.copy_(conns_h, non_blocking=True)
+        obs.copy_(obs_h, non_blocking=True)
+        episode_batched()
+        act_h.copy_(act, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    t_e2e = reduce_max(e0.elapsed_time(e1) / 1e3)
+    h2d = nodes_h.numel() * 4 + conns_h.numel() * 4 + obs_h.numel() * 4
+    d2h = act_h.numel() * 4
+
+    # ---- roofline of the forward kernel: algorithmic bytes per launch
+    hdr = rec.view(POP, -1)[:, :32].cpu().numpy().view(np.uint32)
+    rec_bytes = int(hdr[:, 4].astype(np.int64).sum())                    # used bytes of every record
+    alg_bytes = rec_bytes + POP * I * 4 + POP * O * 4
+    fwd_launch_s = statistics.mean(fw_ms) / 1e3 / S                      # per forward, graph-amortised
+    achieved = alg_bytes / fwd_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "forward_ant_traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("kernel_hash") == kernel_hash():
+                traffic = tj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_batched / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Ant-shaped control: 10000 genomes/GPU, 27 in / 8 out, max 50 nodes / 200 conns, "
+                               "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + "
+                               f"{S} sequential forwards (1 obs/genome/step)",
+                   "l2": "inputs larger than L2 (1.08 GB of observations per bench step)",
+                   "form": "batched: CUDA graph of the steps with programmatic dependent launch",
+                   "launch": {"group": L_batched.group, "tile": L_batched.tile,
+                              "groups_per_block": L_batched.groups_per_block}},
+        "plain": {"value": value_plain, "unit": UNIT, "episodes": n_plain,
+                  "step_p50_ms": float(np.percentile(step_ms, 50)), "step_p99_ms": float(np.percentile(step_ms, 99))},
+        "latency_ms": {"episode_p50": float(np.percentile(ep_ms, 50)), "episode_p99": float(np.percentile(ep_ms, 99)),
+                       "step_mean_batched": statistics.mean(fw_ms) / S},
+        "e2e": {"value": world * POP * S * n_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": n_e2e},
+        "gpu_launches": args.steps * (1 + S),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "kernel": "forward_kernel (batched form, per launch, graph-amortised)",
+                     "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pop, obs.cpu().numpy())
+    cache.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for fn in ("neat_forward.cu", "neat_device.cuh", "neat_internal.h"):
+        with open(os.path.join(ROOT, "paper_2404_01817_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

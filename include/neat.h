@@ -1,0 +1,247 @@
+/*
+ * neat.h -- C ABI of libneat.so: population-wide evaluation of NEAT genomes
+ * on one GB300 (sm_103a).
+ *
+ * The method is the tensorized inference of Section 3.3 ("Tensorized Network
+ * Inference"): a population of networks, each encoded as a NaN-padded node
+ * tensor and connection tensor (Section 3.1, "Tensorized Encodings"), is
+ * first *transformed* once (topological order of the nodes plus the incoming
+ * connections of every node; this library stores a compact per-node list in
+ * place of the dense |N|max x |N|max expanded-connection tensor C_exp), then
+ * *forwarded* on any number of input vectors.  The function names mirror the
+ * genome interface's transform(nodes, conns) / forward(inputs, transformed)
+ * (Appendix "Interfaces", Listing 2).
+ *
+ * Conventions for every call below
+ *   - Pointers named *_dev are DEVICE pointers owned by the caller; pointers
+ *     named *_host are host pointers.  Nothing is retained after return
+ *     except where a call says so.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it and return
+ *     without synchronising; results are ready when the stream reaches them.
+ *   - Return value: NEAT_OK (0) or a negative NEAT_E* code.  On error nothing
+ *     was enqueued and neat_last_error() (thread-local) describes the cause.
+ *   - No call on the forward path allocates device memory.
+ *
+ * Genome encoding (Section 3.1)
+ *   nodes_dev f32 [pop][max_nodes][5]: (key, bias, response, aggregation, activation)
+ *   conns_dev f32 [pop][max_conns][4]: (in key, out key, enabled, weight)
+ *   A node row is present when its key is not NaN; a connection row when its
+ *   in key, out key and enabled flag are not NaN.  Absent (NaN) rows may sit
+ *   anywhere, also between present rows (node or connection removal writes
+ *   NaN into a row, Section 3.2).
+ *   Keys are historical markers: exact integers in [0, 2^24), looked up,
+ *   never used as row indices.  Input j is the node with key j (0 <= j < I),
+ *   output j the node with key I + j (the interface's input_idx = arange(I),
+ *   output_idx = arange(I, I+O)).
+ *   Categorical attributes are stored as integer-valued floats (Section 3.1
+ *   gives tanh = 1, sigmoid = 2):
+ *     activation 0 identity, 1 tanh, 2 sigmoid 1/(1+e^-z), 3 relu max(z,0),
+ *                4 sin, 5 gauss e^(-z^2), 6 abs
+ *     aggregation 0 sum, 1 product, 2 max, 3 mean
+ *   A connection is enabled when its flag is non-zero; disabled connections
+ *   take no part in the order or the forward pass (the C_exp rule maps them
+ *   to NaN).
+ *
+ * Node rule (Section 3.3): f_c(x | w) = w x and
+ *   v[k] = act_k(bias_k + response_k * agg_k(w_c v[src_c] for the enabled
+ *          connections c into k, in ascending connection row)),
+ * the response factor being this library's reading (the paper lists response
+ * among the node hyperparameters, Appendix "Hyperparameters").  An empty
+ * incoming set aggregates to 0.  Input nodes pass their input value through;
+ * their other attributes are ignored.  Arithmetic is IEEE float32; every
+ * node's aggregate is accumulated by one thread in the fixed order above
+ * (sum and mean with fused multiply-add), so a genome's outputs are a
+ * function of the genome and the input alone, whatever the launch shape.
+ */
+#ifndef NEAT_H
+#define NEAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NEAT_API __attribute__((visibility("default")))
+#else
+#define NEAT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ constants */
+
+enum {
+    NEAT_OK = 0,
+    NEAT_EINVAL = -1,      /* bad argument: null pointer, size out of range */
+    NEAT_ENOMEM = -2,      /* a buffer is too small, or host/device allocation failed */
+    NEAT_ECUDA = -3,       /* a CUDA runtime call failed (see neat_last_error) */
+    NEAT_EBUDGET = -4,     /* request can never fit the server's memory budget */
+    NEAT_EAGAIN = -5,      /* not finished yet */
+    NEAT_ETIMEOUT = -6,    /* a bounded wait expired */
+    NEAT_ECANCELLED = -7   /* request was cancelled */
+};
+
+/* Per-genome status word written by neat_transform.  The low byte holds
+ * errors: a genome with any of them is not evaluated and every one of its
+ * outputs is NaN.  Bits 8.. are warnings: the offending rows are ignored and
+ * the genome is evaluated. */
+enum {
+    NEAT_G_CYCLE = 1u,        /* enabled connections form a cycle */
+    NEAT_G_DUPKEY = 2u,       /* two present node rows share a key */
+    NEAT_G_BADKEY = 4u,       /* a key is not an integer in [0, 2^24) */
+    NEAT_G_BADENUM = 8u,      /* activation or aggregation id out of range */
+    NEAT_G_DUPCONN = 16u,     /* two present connections join the same keys */
+    NEAT_G_BADATTR = 32u,     /* NaN bias/response, or NaN weight of an enabled connection */
+    NEAT_G_MISSING_IO = 64u,  /* an input or output key has no node */
+    NEAT_W_DANGLING = 256u,   /* enabled connection to/from an absent key (ignored) */
+    NEAT_W_INTO_INPUT = 512u  /* enabled connection into an input node (ignored) */
+};
+#define NEAT_G_ERROR_MASK 0xffu
+
+/* Limits of this implementation. */
+#define NEAT_MAX_NODES 1024
+#define NEAT_MAX_CONNS 8192
+
+typedef struct neat_dims {
+    int32_t num_inputs;   /* I  >= 0 */
+    int32_t num_outputs;  /* O  >= 1; I + O <= max_nodes */
+    int32_t max_nodes;    /* |N|max, 1..NEAT_MAX_NODES */
+    int32_t max_conns;    /* |C|max, 0..NEAT_MAX_CONNS */
+} neat_dims;
+
+/* ------------------------------------------------- transformed records
+ *
+ * neat_transform writes one record per genome at byte offset g * stride of
+ * the `transformed` buffer (stride = neat_record_stride(d), a multiple of
+ * 128).  A record is packed in topological-position space: position p is the
+ * p-th node of the order; every reference to a node is its position.
+ *
+ *   offset 0   neat_record_header
+ *   offset 32  node entries [n_nodes]      (neat_node_entry, 16 B each)
+ *   off_edge   edge entries [n_edges]      (neat_edge_entry, 8 B each)
+ *   off_level  uint16 level_ptr[n_levels + 1]: level l = positions
+ *              [level_ptr[l], level_ptr[l+1])
+ *   off_io     uint16 in_pos[I] (position of input key j), then
+ *              uint16 out_pos[O] (position of output key I + j)
+ *   used_bytes total bytes written, a multiple of 16
+ * The order is the layered Kahn order: level 0 holds the present nodes with
+ * no enabled incoming connection, level l+1 the nodes whose last incoming
+ * connection comes from level l, and within a level positions follow
+ * ascending node row.  A node's incoming edges are
+ * [edge_begin, edge_begin + edge_count) in ascending connection row.
+ * When the status has an error bit only the header is meaningful
+ * (n_levels = 0).
+ */
+typedef struct neat_record_header {
+    int32_t n_nodes;      /* present node rows */
+    int32_t n_levels;
+    int32_t n_edges;      /* enabled connections kept */
+    uint32_t status;      /* NEAT_G_* / NEAT_W_* bits */
+    uint32_t used_bytes;
+    uint32_t off_edge;
+    uint32_t off_level;
+    uint32_t off_io;
+} neat_record_header;
+
+typedef struct neat_node_entry {
+    float bias;
+    float response;
+    uint16_t edge_begin;
+    uint16_t edge_count;
+    uint8_t activation;   /* 0..6, or 255 for an input node */
+    uint8_t aggregation;  /* 0..3 */
+    uint16_t row;         /* node row in the genome tensor */
+} neat_node_entry;
+
+typedef struct neat_edge_entry {
+    float weight;
+    uint32_t src;         /* position of the source node */
+} neat_edge_entry;
+
+/* Bytes of one genome's record for these dimensions (0 if they are invalid). */
+NEAT_API size_t neat_record_stride(neat_dims d);
+
+/* Bytes of the transformed buffer for `pop` genomes (0 if invalid). */
+NEAT_API size_t neat_transformed_bytes(int32_t pop, neat_dims d);
+
+/*
+ * Transformation stage (Section 3.3): for each of `pop` genomes, check the
+ * rows, resolve keys, build the layered Kahn order and the incoming edge
+ * lists, and write its record into transformed_dev.
+ *   nodes_dev, conns_dev   genome tensors as above (16-byte aligned)
+ *   transformed_dev        >= neat_transformed_bytes(pop, d) bytes, 16-byte aligned
+ *   status_dev             uint32 [pop], may be NULL (the status is also in each header)
+ * Errors: NEAT_EINVAL (null pointer, pop < 0, invalid dims), NEAT_ENOMEM
+ * (transformed_bytes too small), NEAT_ECUDA (launch failed).  Malformed
+ * genomes are not call errors: they are reported in their status word.
+ */
+NEAT_API int neat_transform(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                   void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
+                   void *stream);
+
+/*
+ * Calculation stage (Section 3.3): outputs of every genome on `batch` input
+ * vectors each.
+ *   transformed_dev  records written by neat_transform with the same dims
+ *   inputs_dev       f32 [pop][batch][I]
+ *   outputs_dev      f32 [pop][batch][O] (written; NaN for genomes with an error bit)
+ * The launch shape is chosen from (dims, batch); the results do not depend on it.
+ * Errors: NEAT_EINVAL, NEAT_ECUDA.
+ */
+NEAT_API int neat_forward(const void *transformed_dev, int32_t pop, neat_dims d,
+                 const float *inputs_dev, int32_t batch, float *outputs_dev, void *stream);
+
+/*
+ * Launch shape of the forward kernel.  A work item is (genome, tile of
+ * `tile` input vectors), evaluated by a group of `group` threads: tile
+ * columns times group/tile threads that split each level's nodes.
+ * `groups_per_block` groups share a thread block.  `pdl` != 0 launches with
+ * programmatic dependent launch: the record is staged before the kernel waits
+ * on the previous kernel in the stream, the inputs after.
+ * Constraints: group a power of two in 2..512, tile a power of two <= group,
+ * group * groups_per_block <= 1024.
+ */
+typedef struct neat_launch {
+    int32_t group;
+    int32_t tile;
+    int32_t groups_per_block;
+    int32_t pdl;
+} neat_launch;
+
+/* The launch shape neat_forward uses for (d, batch). */
+NEAT_API int neat_default_launch(neat_dims d, int32_t batch, neat_launch *out_host);
+
+/* neat_forward with an explicit launch shape (NULL = default). */
+NEAT_API int neat_forward_ex(const void *transformed_dev, int32_t pop, neat_dims d,
+                    const float *inputs_dev, int32_t batch, float *outputs_dev,
+                    const neat_launch *launch_host, void *stream);
+
+/*
+ * Steps loop as one CUDA graph: `steps` forwards of the same transformed
+ * population, step s reading inputs_dev + s * in_step_stride floats and
+ * writing outputs_dev + s * out_step_stride floats, each launched with
+ * programmatic dependent launch so that a step stages its records while the
+ * previous step drains.  The graph is built on first use and kept in `*cache`
+ * (opaque, initialise to NULL; freed by neat_steps_cache_destroy); it is
+ * rebuilt when any argument changes.  Enqueued on `stream`.
+ */
+typedef struct neat_steps_cache neat_steps_cache;
+NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_dims d,
+                       const float *inputs_dev, int64_t in_step_stride, int32_t batch,
+                       float *outputs_dev, int64_t out_step_stride, int32_t steps,
+                       const neat_launch *launch_host, neat_steps_cache **cache, void *stream);
+NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
+
+/* Description of the last error on this thread ("" if none). */
+NEAT_API const char *neat_last_error(void);
+
+/* Library version string. */
+NEAT_API const char *neat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEAT_H */

@@ -97,16 +97,17 @@ static int cmp_pair(const void *p, const void *q)
 }
 static int cmp_int(const void *a, const void *b) { return *(const int *)a - *(const int *)b; }
 
-/* row of a key among the sorted (key,row) pairs, or -1 */
+/* lowest row holding a key, among the (key,row) pairs sorted by key then
+ * row, or -1.  (A duplicated key is already an error; taking its lowest row
+ * keeps the remaining status bits of such a genome well defined.) */
 static int lookup(const keyrow_t *map, int n, long key)
 {
-    int lo = 0, hi = n - 1;
-    while (lo <= hi) {
+    int lo = 0, hi = n;                    /* first pair with pair.key >= key */
+    while (lo < hi) {
         int mid = (lo + hi) / 2;
-        if (map[mid].key == key) return map[mid].row;
-        if (map[mid].key < key) lo = mid + 1; else hi = mid - 1;
+        if (map[mid].key < key) lo = mid + 1; else hi = mid;
     }
-    return -1;
+    return (lo < n && map[lo].key == key) ? map[lo].row : -1;
 }
 
 static void genome_alloc(genome_t *g, int I, int O, int Nmax, int Cmax)

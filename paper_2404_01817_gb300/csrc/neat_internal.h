@@ -1,0 +1,68 @@
+// Internal declarations shared by the CUDA translation units of libneat.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/neat.h"
+
+namespace neat {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);   // records and returns NEAT_ECUDA
+int invalid(const char *what);                     // records and returns NEAT_EINVAL
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------ record geometry
+constexpr uint32_t kHeaderBytes = 32;
+constexpr uint32_t kNodeBytes = 16;
+constexpr uint32_t kEdgeBytes = 8;
+constexpr uint8_t kInputAct = 255;
+
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Largest record (all rows present, every connection enabled).
+__host__ __device__ inline uint32_t record_max_bytes(int I, int O, int N, int C)
+{
+    uint32_t off_edge = kHeaderBytes + kNodeBytes * (uint32_t)N;
+    uint32_t off_level = align16(off_edge + kEdgeBytes * (uint32_t)C);
+    uint32_t off_io = align16(off_level + 2u * (uint32_t)(N + 1));
+    return align16(off_io + 2u * (uint32_t)(I + O));
+}
+
+inline size_t record_stride(const neat_dims &d)
+{
+    size_t b = record_max_bytes(d.num_inputs, d.num_outputs, d.max_nodes, d.max_conns);
+    return (b + 127) & ~(size_t)127;
+}
+
+bool dims_ok(const neat_dims &d);
+
+// ---------------------------------------------------------- forward args
+struct ForwardArgs {
+    const uint8_t *rec;      // records, one per genome, `stride` bytes apart
+    size_t stride;
+    const float *x;          // [pop][B][I]
+    float *y;                // [pop][B][O]
+    int pop, I, O, N;
+    int B;                   // input vectors per genome
+    int tile;                // columns per work item
+    int tiles;               // ceil(B / tile)
+    int rec_words;           // 16-byte words of shared memory reserved for a record
+    int val_floats;          // floats of shared memory for node values (N * tile, rounded to 4)
+};
+
+// Launch one forward over a single population (defined in neat_forward.cu).
+int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s);
+int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d,
+                      const float *inputs, int32_t batch, float *outputs,
+                      const neat_launch &L, ForwardArgs *out);
+int check_launch(const neat_launch &L);
+
+}  // namespace neat

@@ -1,0 +1,348 @@
+// Transformation stage of tensorized NEAT inference (Section 3.3): one thread
+// block per genome turns the padded node/connection tensors (Section 3.1)
+// into a record holding the layered Kahn order and, in place of the dense
+// expanded-connection tensor C_exp, the enabled incoming edges of every node
+// packed by destination position (layout in include/neat.h).
+//
+// All per-genome work happens in shared memory:
+//   1. node rows: presence, key and attribute checks; (key,row) pairs sorted
+//      (bitonic) so keys resolve to rows by binary search;
+//   2. connection rows: checks, endpoint lookup, duplicate (in,out) detection
+//      by sorting the key pairs;
+//   3. layered Kahn: one pass over the active edges per level, removing the
+//      edges of level L with shared-memory atomics; a node whose count hits
+//      zero joins level L+1;
+//   4. positions = rank of (level, row); edges sorted by (destination
+//      position, connection row), which fixes each node's summation order.
+#include "neat_device.cuh"
+#include "neat_internal.h"
+
+namespace neat {
+namespace {
+
+struct TransformArgs {
+    const float *nodes;
+    const float *conns;
+    uint8_t *out;
+    uint32_t *status;
+    size_t stride;
+    int pop, I, O, N, C;
+    int Np2, Cp2;   // powers of two >= N and >= max(C, 1)
+};
+
+__device__ __forceinline__ bool is_key(float k)
+{
+    return !isnan(k) && k >= 0.0f && k < 16777216.0f && floorf(k) == k;
+}
+
+__device__ __forceinline__ bool is_enum(float v, int n)
+{
+    return !isnan(v) && floorf(v) == v && v >= 0.0f && v < (float)n;
+}
+
+// In-place ascending bitonic sort of n2 (a power of two) keys; every thread
+// of the block must call it.
+template <typename T>
+__device__ void bitonic_sort(T *a, int n2)
+{
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const T x = a[i], y = a[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Lowest row holding `key` among the n sorted (key << 32 | row) pairs, or -1.
+__device__ int lookup_row(const unsigned long long *map, int n, uint32_t key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint32_t)(map[mid] >> 32) < key) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && (uint32_t)(map[lo] >> 32) == key) ? (int)(map[lo] & 0xffffffffu) : -1;
+}
+
+__host__ __device__ inline size_t transform_smem_bytes(int N, int C, int I, int O, int Np2, int Cp2)
+{
+    size_t b = 8u * (size_t)Np2 + 8u * (size_t)Cp2;          // keymap, pairkey
+    b += 4u * (size_t)(5 * N + I + O);                        // level, indeg, cnt, pos, ebeg, io_row
+    b += 2u * 2u * (size_t)C;                                 // src_row, dst_row
+    return (b + 15u) & ~(size_t)15u;
+}
+
+__global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int g = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int N = a.N, C = a.C, I = a.I, O = a.O;
+
+    unsigned long long *keymap = reinterpret_cast<unsigned long long *>(sm);
+    unsigned long long *pairkey = keymap + a.Np2;
+    int *level = reinterpret_cast<int *>(pairkey + a.Cp2);   // -2 absent, -1 unplaced
+    int *indeg = level + N;
+    int *cnt = indeg + N;
+    int *pos_of_row = cnt + N;
+    int *ebeg = pos_of_row + N;
+    int *io_row = ebeg + N;
+    short *src_row = reinterpret_cast<short *>(io_row + I + O);
+    short *dst_row = src_row + C;
+
+    __shared__ unsigned int st;
+    __shared__ int n_present, n_edges, max_level, changed;
+    if (tid == 0) {
+        st = 0;
+        n_present = 0;
+        n_edges = 0;
+        max_level = -1;
+    }
+    const float *nd = a.nodes + (size_t)g * N * 5;
+    const float4 *cn = reinterpret_cast<const float4 *>(a.conns + (size_t)g * C * 4);
+    for (int r = tid; r < a.Np2; r += nt) keymap[r] = ~0ull;
+    for (int c = tid; c < a.Cp2; c += nt) pairkey[c] = ~0ull;
+    __syncthreads();
+
+    // 1. node rows (Section 3.1 encoding; an absent row is NaN)
+    unsigned int lst = 0;
+    for (int r = tid; r < N; r += nt) {
+        const float k = __ldg(nd + r * 5);
+        indeg[r] = 0;
+        level[r] = -2;
+        if (isnan(k)) continue;
+        if (!is_key(k)) { lst |= NEAT_G_BADKEY; continue; }
+        const float bias = __ldg(nd + r * 5 + 1), resp = __ldg(nd + r * 5 + 2);
+        const float agg = __ldg(nd + r * 5 + 3), act = __ldg(nd + r * 5 + 4);
+        if (!is_enum(agg, 4) || !is_enum(act, 7)) lst |= NEAT_G_BADENUM;
+        if (isnan(bias) || isnan(resp)) lst |= NEAT_G_BADATTR;
+        level[r] = -1;
+        keymap[r] = ((unsigned long long)(uint32_t)k << 32) | (unsigned)r;
+        atomicAdd(&n_present, 1);
+    }
+    if (lst) atomicOr(&st, lst);
+    __syncthreads();
+    bitonic_sort(keymap, a.Np2);
+    const int n = n_present;
+
+    lst = 0;
+    for (int i = tid + 1; i < n; i += nt)
+        if ((keymap[i] >> 32) == (keymap[i - 1] >> 32)) lst |= NEAT_G_DUPKEY;
+    for (int j = tid; j < I + O; j += nt) {
+        const int r = lookup_row(keymap, n, (uint32_t)j);
+        io_row[j] = r;
+        if (r < 0) lst |= NEAT_G_MISSING_IO;
+    }
+
+    // 2. connection rows; disabled ones only count towards duplicate pairs
+    for (int c = tid; c < C; c += nt) {
+        src_row[c] = dst_row[c] = -1;
+        const float4 row = __ldg(cn + c);
+        if (isnan(row.x) || isnan(row.y) || isnan(row.z)) continue;
+        if (!is_key(row.x) || !is_key(row.y)) { lst |= NEAT_G_BADKEY; continue; }
+        const uint32_t ki = (uint32_t)row.x, ko = (uint32_t)row.y;
+        pairkey[c] = ((unsigned long long)ki << 24) | ko;
+        if (row.z == 0.0f) continue;
+        if (isnan(row.w)) lst |= NEAT_G_BADATTR;
+        const int s = lookup_row(keymap, n, ki), d = lookup_row(keymap, n, ko);
+        if (s < 0 || d < 0) { lst |= NEAT_W_DANGLING; continue; }
+        if (ko < (uint32_t)I) { lst |= NEAT_W_INTO_INPUT; continue; }
+        src_row[c] = (short)s;
+        dst_row[c] = (short)d;
+        atomicAdd(&indeg[d], 1);
+        atomicAdd(&n_edges, 1);
+    }
+    if (lst) atomicOr(&st, lst);
+    __syncthreads();
+    bitonic_sort(pairkey, a.Cp2);
+
+    lst = 0;
+    for (int i = tid + 1; i < a.Cp2; i += nt)
+        if (pairkey[i] != ~0ull && pairkey[i] == pairkey[i - 1]) lst |= NEAT_G_DUPCONN;
+    // 3. layered Kahn: level 0 = present nodes without enabled incoming edges
+    for (int r = tid; r < N; r += nt) {
+        cnt[r] = indeg[r];
+        if (level[r] == -1 && indeg[r] == 0) level[r] = 0;
+    }
+    if (lst) atomicOr(&st, lst);
+    for (int L = 0;; ++L) {
+        if (tid == 0) changed = 0;
+        __syncthreads();
+        for (int c = tid; c < C; c += nt) {
+            const int d = dst_row[c];
+            if (d >= 0 && level[src_row[c]] == L) {
+                if (atomicSub(&indeg[d], 1) == 1) {
+                    level[d] = L + 1;
+                    changed = 1;
+                }
+            }
+        }
+        __syncthreads();
+        const int more = changed;
+        __syncthreads();
+        if (!more) break;
+    }
+    lst = 0;
+    int lmax = -1;
+    for (int r = tid; r < N; r += nt) {
+        if (level[r] == -1) lst |= NEAT_G_CYCLE;
+        lmax = max(lmax, level[r]);
+    }
+    if (lst) atomicOr(&st, lst);
+    atomicMax(&max_level, lmax);
+    __syncthreads();
+
+    const uint32_t status = st;
+    uint8_t *rec = a.out + (size_t)g * a.stride;
+    if (status & NEAT_G_ERROR_MASK) {
+        if (tid == 0) {
+            uint4 *h = reinterpret_cast<uint4 *>(rec);
+            h[0] = make_uint4((unsigned)n, 0u, 0u, status);
+            h[1] = make_uint4(kHeaderBytes, kHeaderBytes, kHeaderBytes, kHeaderBytes);
+            if (a.status) a.status[g] = status;
+        }
+        return;
+    }
+
+    // 4. positions: rank of (level, row)
+    const int nl = max_level + 1;
+    const int E = n_edges;
+    const uint32_t off_edge = kHeaderBytes + kNodeBytes * (uint32_t)n;
+    const uint32_t off_level = align16(off_edge + kEdgeBytes * (uint32_t)E);
+    const uint32_t off_io = align16(off_level + 2u * (uint32_t)(nl + 1));
+    const uint32_t used = align16(off_io + 2u * (uint32_t)(I + O));
+
+    uint32_t *ordkey = reinterpret_cast<uint32_t *>(keymap);
+    for (int r = tid; r < a.Np2; r += nt)
+        ordkey[r] = (r < N && level[r] >= 0) ? (((uint32_t)level[r] << 11) | (uint32_t)r) : 0xffffffffu;
+    __syncthreads();
+    bitonic_sort(ordkey, a.Np2);
+    uint16_t *lev_out = reinterpret_cast<uint16_t *>(rec + off_level);
+    for (int p = tid; p < n; p += nt) {
+        const uint32_t key = ordkey[p];
+        pos_of_row[key & 0x7ffu] = p;
+        if (p == 0 || (ordkey[p - 1] >> 11) != (key >> 11)) lev_out[key >> 11] = (uint16_t)p;
+    }
+    if (tid == 0) lev_out[nl] = (uint16_t)n;
+    uint32_t *edgekey = reinterpret_cast<uint32_t *>(pairkey);
+    __syncthreads();
+    for (int c = tid; c < a.Cp2; c += nt)
+        edgekey[c] = (c < C && dst_row[c] >= 0)
+                         ? (((uint32_t)pos_of_row[dst_row[c]] << 13) | (uint32_t)c) : 0xffffffffu;
+    for (int p = tid; p < N; p += nt) ebeg[p] = 0;
+    __syncthreads();
+    bitonic_sort(edgekey, a.Cp2);
+
+    // 5. edges in (destination position, connection row) order
+    uint2 *edges = reinterpret_cast<uint2 *>(rec + off_edge);
+    for (int k = tid; k < E; k += nt) {
+        const uint32_t key = edgekey[k];
+        const int c = (int)(key & 0x1fffu);
+        const int dp = (int)(key >> 13);
+        if (k == 0 || (edgekey[k - 1] >> 13) != (uint32_t)dp) ebeg[dp] = k;
+        const float w = __ldg(a.conns + ((size_t)g * C + c) * 4 + 3);
+        edges[k] = make_uint2(__float_as_uint(w), (uint32_t)pos_of_row[src_row[c]]);
+    }
+    __syncthreads();
+
+    // 6. node entries by position, io positions, header
+    uint4 *nodes_out = reinterpret_cast<uint4 *>(rec + kHeaderBytes);
+    for (int p = tid; p < n; p += nt) {
+        const int r = (int)(ordkey[p] & 0x7ffu);
+        const float key = __ldg(nd + r * 5);
+        const float bias = __ldg(nd + r * 5 + 1), resp = __ldg(nd + r * 5 + 2);
+        const uint32_t agg = (uint32_t)__ldg(nd + r * 5 + 3);
+        const uint32_t act = key < (float)I ? (uint32_t)kInputAct : (uint32_t)__ldg(nd + r * 5 + 4);
+        nodes_out[p] = make_uint4(__float_as_uint(bias), __float_as_uint(resp),
+                                  (uint32_t)ebeg[p] | ((uint32_t)cnt[r] << 16),
+                                  act | (agg << 8) | ((uint32_t)r << 16));
+    }
+    uint16_t *io_out = reinterpret_cast<uint16_t *>(rec + off_io);
+    for (int j = tid; j < I + O; j += nt) io_out[j] = (uint16_t)pos_of_row[io_row[j]];
+    if (tid == 0) {
+        uint4 *h = reinterpret_cast<uint4 *>(rec);
+        h[0] = make_uint4((unsigned)n, (unsigned)nl, (unsigned)E, status);
+        h[1] = make_uint4(used, off_edge, off_level, off_io);
+        if (a.status) a.status[g] = status;
+    }
+}
+
+int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+}  // namespace neat
+
+using namespace neat;
+
+extern "C" size_t neat_record_stride(neat_dims d)
+{
+    return dims_ok(d) ? record_stride(d) : 0;
+}
+
+extern "C" size_t neat_transformed_bytes(int32_t pop, neat_dims d)
+{
+    if (!dims_ok(d) || pop < 0) return 0;
+    return record_stride(d) * (size_t)pop;
+}
+
+extern "C" int neat_transform(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                              void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
+                              void *stream)
+{
+    clear_error();
+    if (!dims_ok(d)) return invalid("neat_transform: invalid dims");
+    if (pop < 0) return invalid("neat_transform: pop < 0");
+    if (pop == 0) return NEAT_OK;
+    if (!nodes_dev || !conns_dev || !transformed_dev) return invalid("neat_transform: null pointer");
+    if ((reinterpret_cast<uintptr_t>(conns_dev) & 15u) || (reinterpret_cast<uintptr_t>(transformed_dev) & 15u))
+        return invalid("neat_transform: conns and transformed must be 16-byte aligned");
+    const size_t stride = record_stride(d);
+    if (transformed_bytes < stride * (size_t)pop) {
+        set_error("neat_transform: transformed buffer too small");
+        return NEAT_ENOMEM;
+    }
+    TransformArgs a;
+    a.nodes = nodes_dev;
+    a.conns = conns_dev;
+    a.out = static_cast<uint8_t *>(transformed_dev);
+    a.status = status_dev;
+    a.stride = stride;
+    a.pop = pop;
+    a.I = d.num_inputs;
+    a.O = d.num_outputs;
+    a.N = d.max_nodes;
+    a.C = d.max_conns;
+    a.Np2 = next_pow2(a.N);
+    a.Cp2 = next_pow2(a.C > 0 ? a.C : 1);
+    const size_t smem = transform_smem_bytes(a.N, a.C, a.I, a.O, a.Np2, a.Cp2);
+    const int threads = (a.N <= 64 && a.C <= 512) ? 128 : (a.N <= 256 && a.C <= 2048 ? 256 : 512);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)transform_smem_bytes(NEAT_MAX_NODES, NEAT_MAX_CONNS, 0,
+                                                                       NEAT_MAX_NODES, NEAT_MAX_NODES,
+                                                                       NEAT_MAX_CONNS));
+        if (e != cudaSuccess) return cuda_fail(e, "neat_transform: cudaFuncSetAttribute");
+        attr_set = true;
+    }
+    transform_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_transform: launch");
+    return NEAT_OK;
+}

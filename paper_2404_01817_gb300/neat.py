@@ -1,0 +1,241 @@
+"""Python binding of libneat.so (include/neat.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; PyTorch provides
+device memory (``tensor.data_ptr()``) and streams.  Nothing is computed in
+Python: if the CUDA library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libneat.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                      f"g.build()\"` (needs nvcc); there is no fallback implementation")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NEAT_OK, NEAT_EINVAL, NEAT_ENOMEM, NEAT_ECUDA, NEAT_EBUDGET, NEAT_EAGAIN, NEAT_ETIMEOUT, NEAT_ECANCELLED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+G_CYCLE, G_DUPKEY, G_BADKEY, G_BADENUM, G_DUPCONN, G_BADATTR, G_MISSING_IO = 1, 2, 4, 8, 16, 32, 64
+W_DANGLING, W_INTO_INPUT = 256, 512
+G_ERROR_MASK = 0xFF
+MAX_NODES, MAX_CONNS = 1024, 8192
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("num_inputs", ctypes.c_int32), ("num_outputs", ctypes.c_int32),
+                ("max_nodes", ctypes.c_int32), ("max_conns", ctypes.c_int32)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("groups_per_block", ctypes.c_int32), ("pdl", ctypes.c_int32)]
+
+    def __repr__(self):
+        return f"Launch(group={self.group}, tile={self.tile}, groups_per_block={self.groups_per_block}, pdl={self.pdl})"
+
+
+_P = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+_sig = {
+    "neat_record_stride": (ctypes.c_size_t, [Dims]),
+    "neat_transformed_bytes": (ctypes.c_size_t, [_i32, Dims]),
+    "neat_transform": (ctypes.c_int, [_P, _P, _i32, Dims, _P, ctypes.c_size_t, _P, _P]),
+    "neat_forward": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, _P]),
+    "neat_default_launch": (ctypes.c_int, [Dims, _i32, ctypes.POINTER(Launch)]),
+    "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
+    "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
+                                          ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
+    "neat_steps_cache_destroy": (None, [_P]),
+    "neat_last_error": (ctypes.c_char_p, []),
+    "neat_version": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class NeatError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where} failed with {code}: {last_error()}")
+        self.code = code
+
+
+def last_error() -> str:
+    return _lib.neat_last_error().decode()
+
+
+def version() -> str:
+    return _lib.neat_version().decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != NEAT_OK:
+        raise NeatError(code, where)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def dims(num_inputs: int, num_outputs: int, max_nodes: int, max_conns: int) -> Dims:
+    return Dims(num_inputs, num_outputs, max_nodes, max_conns)
+
+
+def neat_record_stride(d: Dims) -> int:
+    return _lib.neat_record_stride(d)
+
+
+def neat_transformed_bytes(pop: int, d: Dims) -> int:
+    return _lib.neat_transformed_bytes(pop, d)
+
+
+def neat_default_launch(d: Dims, batch: int) -> Launch:
+    L = Launch()
+    _check(_lib.neat_default_launch(d, batch, ctypes.byref(L)), "neat_default_launch")
+    return L
+
+
+def neat_transform(nodes, conns, d: Dims, transformed=None, status=None, stream=None):
+    """Transform a population (torch CUDA tensors f32 [P][Nmax][5], [P][Cmax][4]).
+
+    Returns (transformed uint8 tensor, status int32 tensor [P])."""
+    import torch
+    pop = nodes.shape[0]
+    assert nodes.is_cuda and nodes.dtype == torch.float32 and nodes.is_contiguous()
+    assert conns.is_cuda and conns.dtype == torch.float32 and conns.is_contiguous()
+    assert tuple(nodes.shape[1:]) == (d.max_nodes, 5) and tuple(conns.shape[1:]) == (d.max_conns, 4)
+    nbytes = neat_transformed_bytes(pop, d)
+    if transformed is None:
+        transformed = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=nodes.device)
+    if status is None:
+        status = torch.empty(max(pop, 1), dtype=torch.int32, device=nodes.device)
+    _check(_lib.neat_transform(_ptr(nodes), _ptr(conns), pop, d, _ptr(transformed),
+                               transformed.numel() * transformed.element_size(), _ptr(status),
+                               _stream(stream)), "neat_transform")
+    return transformed, status[:pop]
+
+
+def neat_forward(transformed, pop: int, d: Dims, inputs, outputs=None, launch: Launch | None = None,
+                 stream=None):
+    """Outputs f32 [P][B][O] of a transformed population on inputs f32 [P][B][I]."""
+    import torch
+    assert inputs.dtype == torch.float32 and inputs.is_contiguous()
+    batch = inputs.shape[1]
+    assert inputs.shape[0] == pop and inputs.shape[2] == d.num_inputs
+    if outputs is None:
+        outputs = torch.empty((pop, batch, d.num_outputs), dtype=torch.float32, device=inputs.device)
+    code = _lib.neat_forward_ex(_ptr(transformed), pop, d, _ptr(inputs), batch, _ptr(outputs),
+                                ctypes.byref(launch) if launch is not None else None, _stream(stream))
+    _check(code, "neat_forward")
+    return outputs
+
+
+class StepsCache:
+    """Owner of the CUDA graph that neat_forward_steps builds and replays."""
+
+    def __init__(self):
+        self.handle = _P(None)
+
+    def close(self):
+        if self.handle.value:
+            _lib.neat_steps_cache_destroy(self.handle)
+            self.handle = _P(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def neat_forward_steps(transformed, pop: int, d: Dims, inputs, outputs, cache: StepsCache,
+                       launch: Launch | None = None, stream=None):
+    """Run ``steps`` forwards as one CUDA graph: inputs f32 [S][P][B][I] ->
+    outputs f32 [S][P][B][O] (step s reads inputs[s], writes outputs[s])."""
+    steps, P, B = inputs.shape[0], inputs.shape[1], inputs.shape[2]
+    assert P == pop and outputs.shape[:3] == (steps, pop, B)
+    assert inputs.is_contiguous() and outputs.is_contiguous()
+    code = _lib.neat_forward_steps(_ptr(transformed), pop, d, _ptr(inputs), P * B * d.num_inputs, B,
+                                   _ptr(outputs), P * B * d.num_outputs, steps,
+                                   ctypes.byref(launch) if launch is not None else None,
+                                   ctypes.byref(cache.handle), _stream(stream))
+    _check(code, "neat_forward_steps")
+    return outputs
+
+
+# ----------------------------------------------------------- record decoding
+
+@dataclass
+class Decoded:
+    """Host view of transformed records, in the oracle's terms (node rows)."""
+    n_nodes: np.ndarray      # [P]
+    n_levels: np.ndarray     # [P]
+    n_edges: np.ndarray      # [P]
+    status: np.ndarray       # [P] uint32
+    order: np.ndarray        # [P][Nmax] node row per position, -1 pad
+    level_ptr: np.ndarray    # [P][Nmax+1] (padded with n_nodes)
+    in_ptr: np.ndarray       # [P][Nmax+1] by position (padded with n_edges)
+    in_src: np.ndarray       # [P][Cmax] source node row, -1 pad
+    in_w: np.ndarray         # [P][Cmax] float32 weights, 0 pad
+    in_pos: np.ndarray       # [P][I]
+    out_pos: np.ndarray      # [P][O]
+
+
+def decode_records(buf: np.ndarray, pop: int, d: Dims) -> Decoded:
+    """Unpack ``pop`` records (a host uint8 copy of the transformed buffer)
+    following the layout documented in include/neat.h."""
+    stride = neat_record_stride(d)
+    N, C, I, O = d.max_nodes, d.max_conns, d.num_inputs, d.num_outputs
+    buf = np.ascontiguousarray(buf[: stride * pop]).reshape(pop, stride)
+    hdr = buf[:, :32].copy().view(np.uint32).reshape(pop, 8)
+    out = Decoded(n_nodes=hdr[:, 0].astype(np.int32), n_levels=hdr[:, 1].astype(np.int32),
+                  n_edges=hdr[:, 2].astype(np.int32), status=hdr[:, 3].copy(),
+                  order=np.full((pop, N), -1, np.int32), level_ptr=np.zeros((pop, N + 1), np.int32),
+                  in_ptr=np.zeros((pop, N + 1), np.int32), in_src=np.full((pop, C), -1, np.int32),
+                  in_w=np.zeros((pop, C), np.float32), in_pos=np.zeros((pop, I), np.int32),
+                  out_pos=np.zeros((pop, O), np.int32))
+    for g in range(pop):
+        n, nl, E = int(hdr[g, 0]), int(hdr[g, 1]), int(hdr[g, 2])
+        if hdr[g, 3] & G_ERROR_MASK:
+            continue
+        off_edge, off_level, off_io = int(hdr[g, 5]), int(hdr[g, 6]), int(hdr[g, 7])
+        nodes = buf[g, 32:32 + 16 * n].copy()
+        rows = nodes.view(np.uint16).reshape(n, 8)[:, 7].astype(np.int32)
+        ebeg = nodes.view(np.uint16).reshape(n, 8)[:, 4].astype(np.int32)
+        ecnt = nodes.view(np.uint16).reshape(n, 8)[:, 5].astype(np.int32)
+        out.order[g, :n] = rows
+        lev = buf[g, off_level:off_level + 2 * (nl + 1)].copy().view(np.uint16).astype(np.int32)
+        out.level_ptr[g, :nl + 1] = lev
+        out.level_ptr[g, nl + 1:] = n
+        starts = np.concatenate([[0], np.cumsum(ecnt)])
+        out.in_ptr[g, :n] = starts[:-1]
+        out.in_ptr[g, n:] = E
+        assert np.all(ebeg[ecnt > 0] + ecnt[ecnt > 0] <= E)
+        edges = buf[g, off_edge:off_edge + 8 * E].copy()
+        out.in_w[g, :E] = edges.view(np.float32).reshape(E, 2)[:, 0]
+        src_pos = edges.view(np.uint32).reshape(E, 2)[:, 1].astype(np.int64)
+        out.in_src[g, :E] = rows[src_pos]
+        io = buf[g, off_io:off_io + 2 * (I + O)].copy().view(np.uint16).astype(np.int32)
+        out.in_pos[g] = io[:I]
+        out.out_pos[g] = io[I:]
+        # edge_begin/edge_count must tile [0, E) in position order
+        assert starts[-1] == E and np.array_equal(starts[:-1][ecnt > 0], ebeg[ecnt > 0])
+    return out

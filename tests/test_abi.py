@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports what include/neat.h declares.
+
+CPU only: these tests make no CUDA call that needs a device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2404_01817_gb300 import build
+    return build.build()
+
+
+def declared_symbols():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^NEAT_API[^(]*?\b(neat_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = set(declared_symbols())
+    for required in ("neat_transform", "neat_forward", "neat_transformed_bytes", "neat_forward_steps",
+                     "neat_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(lib_path):
+    from paper_2404_01817_gb300 import neat
+    d = neat.dims(27, 8, 50, 200)
+    stride = neat.neat_record_stride(d)
+    assert stride % 128 == 0 and stride >= 32 + 16 * 50 + 8 * 200
+    assert neat.neat_transformed_bytes(10000, d) == 10000 * stride
+    assert neat.neat_record_stride(neat.dims(0, 1, 1025, 4)) == 0          # too many nodes
+    assert neat.neat_record_stride(neat.dims(3, 0, 10, 4)) == 0            # no outputs
+    assert neat.neat_record_stride(neat.dims(8, 4, 10, 4)) == 0            # I + O > Nmax
+    assert neat.neat_record_stride(neat.dims(1, 1, 4, 8193)) == 0          # too many conns
+    for B in (1, 4, 64, 256):
+        for N in (10, 50, 256, 1024):
+            L = neat.neat_default_launch(neat.dims(4, 2, N, 4 * N), B)
+            assert L.group >= L.tile and L.group * L.groups_per_block <= 1024
+
+
+def test_argument_errors_do_not_touch_the_device(lib_path):
+    from paper_2404_01817_gb300 import neat
+    lib = neat._lib
+    d = neat.dims(3, 1, 10, 20)
+    assert lib.neat_transform(None, None, 4, d, None, 0, None, None) == neat.NEAT_EINVAL
+    assert "null" in neat.last_error()
+    assert lib.neat_transform(None, None, 4, neat.dims(3, 1, 2000, 20), None, 0, None, None) == neat.NEAT_EINVAL
+    assert lib.neat_transform(16, 16, 4, d, 16, 10, None, None) == neat.NEAT_ENOMEM
+    bad = neat.Launch(3, 1, 1, 0)
+    assert lib.neat_forward_ex(16, 1, d, 16, 1, 16, ctypes.byref(bad), None) == neat.NEAT_EINVAL
+    assert lib.neat_transform(None, None, 0, d, None, 0, None, None) == neat.NEAT_OK   # empty population
