@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--env-steps", type=int, default=ENV_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
     return ap.parse_args()
 
 
@@ -212,8 +214,8 @@ def main():
     status = torch.empty(POP, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     cache = neat.StepsCache()
-    L_plain = neat.neat_default_launch(d, 1)
-    L_batched = neat.neat_default_launch(d, 1)
+    L_plain = neat.neat_default_launch(POP, d, 1)
+    L_batched = neat.neat_default_launch(POP, d, 1)
     L_batched.pdl = 1
 
     def episode_batched():
@@ -240,6 +242,16 @@ def main():
         t = torch.tensor([x], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
+
+    if args.profile:
+        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        for s in range(3):
+            neat.neat_forward(rec, POP, d, obs[s], act[s], launch=L_plain, stream=stream)
+        neat.neat_forward_steps(rec, POP, d, obs[:8], act[:8], cache, launch=L_batched, stream=stream)
+        torch.cuda.synchronize(dev)
+        cache.close()
+        print("profile case done", flush=True)
+        return
 
     # ---- warm-up (also builds the CUDA graph)
     for _ in range(args.warmup):

@@ -49,10 +49,14 @@
  * the response factor being this library's reading (the paper lists response
  * among the node hyperparameters, Appendix "Hyperparameters").  An empty
  * incoming set aggregates to 0.  Input nodes pass their input value through;
- * their other attributes are ignored.  Arithmetic is IEEE float32; every
- * node's aggregate is accumulated by one thread in the fixed order above
- * (sum and mean with fused multiply-add), so a genome's outputs are a
- * function of the genome and the input alone, whatever the launch shape.
+ * their other attributes are ignored.
+ * Arithmetic is IEEE float32 in a fixed order: a node's incoming edges
+ * (ascending connection row) are dealt round-robin into four partials,
+ * partial k holding edges k, k+4, k+8, ... accumulated in that order (sum and
+ * mean with fused multiply-add), and the aggregate is ((p0 . p1) . (p2 . p3))
+ * for the aggregation's operation "." (then / count for the mean).  The order
+ * depends on the genome alone, so its outputs are a function of the genome
+ * and the input, bit for bit, whatever the launch shape or co-scheduled work.
  */
 #ifndef NEAT_H
 #define NEAT_H
@@ -135,10 +139,13 @@ typedef struct neat_dims {
  * (n_levels = 0).
  */
 typedef struct neat_record_header {
-    int32_t n_nodes;      /* present node rows */
-    int32_t n_levels;
+    uint16_t n_nodes;     /* present node rows */
+    uint16_t n_levels;
     int32_t n_edges;      /* enabled connections kept */
     uint32_t status;      /* NEAT_G_* / NEAT_W_* bits */
+    uint8_t uniform_activation;   /* activation id shared by every non-input node, else 255 */
+    uint8_t uniform_aggregation;  /* aggregation id shared by every non-input node, else 255 */
+    uint16_t lead_inputs; /* positions 0 .. lead_inputs-1 are all input nodes */
     uint32_t used_bytes;
     uint32_t off_edge;
     uint32_t off_level;
@@ -200,7 +207,7 @@ NEAT_API int neat_forward(const void *transformed_dev, int32_t pop, neat_dims d,
  * `groups_per_block` groups share a thread block.  `pdl` != 0 launches with
  * programmatic dependent launch: the record is staged before the kernel waits
  * on the previous kernel in the stream, the inputs after.
- * Constraints: group a power of two in 2..512, tile a power of two <= group,
+ * Constraints: group a power of two in 1..1024, tile a power of two <= group,
  * group * groups_per_block <= 1024.
  */
 typedef struct neat_launch {
@@ -208,10 +215,13 @@ typedef struct neat_launch {
     int32_t tile;
     int32_t groups_per_block;
     int32_t pdl;
+    int32_t split;   /* tile == 1: at most this many threads (1, 2 or 4) share one node's edges,
+                        chosen per level from its width; else ignored (1) */
 } neat_launch;
 
-/* The launch shape neat_forward uses for (d, batch). */
-NEAT_API int neat_default_launch(neat_dims d, int32_t batch, neat_launch *out_host);
+/* The launch shape neat_forward uses for (pop, d, batch): the smallest
+ * number of waves on the current device, genomes spread evenly over its SMs. */
+NEAT_API int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat_launch *out_host);
 
 /* neat_forward with an explicit launch shape (NULL = default). */
 NEAT_API int neat_forward_ex(const void *transformed_dev, int32_t pop, neat_dims d,
@@ -233,6 +243,14 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
                        float *outputs_dev, int64_t out_step_stride, int32_t steps,
                        const neat_launch *launch_host, neat_steps_cache **cache, void *stream);
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
+
+/*
+ * Device error word of the forward kernels: bit 0 is set when a bounded
+ * on-device wait (the record copy into shared memory) ran out; the affected
+ * outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
+ * Synchronous (a device-to-host copy on the legacy stream).
+ */
+NEAT_API int neat_device_error(int32_t clear, uint32_t *out_host);
 
 /* Description of the last error on this thread ("" if none). */
 NEAT_API const char *neat_last_error(void);

@@ -13,150 +13,128 @@
 // the record's fixed order, so results are independent of the launch shape.
 // The path is bound by on-chip latency and L2/HBM bandwidth, not by any
 // dense contraction, so no tensor-core instruction is involved.
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_item.cuh"
 
 namespace neat {
 namespace {
 
-template <int G>
-__device__ __forceinline__ void group_sync(int gi)
-{
-    if constexpr (G < 32) {
-        const unsigned base = (threadIdx.x & 31u) & ~(unsigned)(G - 1);
-        __syncwarp(((1u << G) - 1u) << base);
-    } else if constexpr (G == 32) {
-        __syncwarp();
-    } else {
-        if (blockDim.x == G) __syncthreads();
-        else asm volatile("bar.sync %0, %1;" ::"r"(gi + 1), "r"(G) : "memory");
-    }
-}
+// Library error word: a bounded wait in a forward kernel expired.
+__device__ unsigned int g_forward_error;
 
-// One node of the node rule for column `col` of the tile.
-__device__ __forceinline__ void eval_node(const uint4 ne, const uint2 *__restrict__ edges,
-                                          float *__restrict__ v, int p, int T, int col)
-{
-    const uint32_t act = ne.w & 0xffu;
-    if (act == kInputAct) return;
-    const uint32_t agg = (ne.w >> 8) & 0xffu;
-    const uint32_t eb = ne.z & 0xffffu, ec = ne.z >> 16;
-    const uint2 *e = edges + eb;
-    float acc = 0.0f;
-    if (agg == 0u || agg == 3u) {
-#pragma unroll 4
-        for (uint32_t i = 0; i < ec; ++i) {
-            const uint2 t = e[i];
-            acc = fmaf(__uint_as_float(t.x), v[t.y * T + col], acc);
-        }
-        if (agg == 3u && ec) acc = acc / (float)ec;
-    } else if (ec) {
-        const uint2 t0 = e[0];
-        acc = __uint_as_float(t0.x) * v[t0.y * T + col];
-        if (agg == 1u) {
-            for (uint32_t i = 1; i < ec; ++i) {
-                const uint2 t = e[i];
-                acc = acc * (__uint_as_float(t.x) * v[t.y * T + col]);
-            }
-        } else {
-            for (uint32_t i = 1; i < ec; ++i) {
-                const uint2 t = e[i];
-                acc = fmaxf(acc, __uint_as_float(t.x) * v[t.y * T + col]);
-            }
-        }
-    }
-    const float z = fmaf(__uint_as_float(ne.y), acc, __uint_as_float(ne.x));
-    v[p * T + col] = activate(act, z);
-}
+constexpr int kInputRegs = 8;   // inputs prefetched into registers per thread
 
-template <int G, bool PDL>
+// One work item per group of a.group threads.  T1: one input vector per
+// genome (tile 1), the case of a control loop that steps every genome once.
+template <bool PDL, bool T1>
 __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
 {
     extern __shared__ __align__(16) uint4 smem[];
-    const int gpb = blockDim.x / G;
-    const int gi = threadIdx.x / G;
-    const int lane = threadIdx.x % G;
-    uint4 *srec = smem + (size_t)gi * (a.rec_words + a.val_floats / 4);
+    const int G = a.group, lgG = ilog2(G);
+    const int gpb = blockDim.x >> lgG;
+    const int gi = threadIdx.x >> lgG;
+    const int lane = threadIdx.x & (G - 1);
+    // [mbarriers of the block's groups][group 0: record | values][group 1: ...]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    uint4 *srec = smem + (gpb + 1) / 2 + (size_t)gi * (a.rec_words + a.val_floats / 4);
     float *v = reinterpret_cast<float *>(srec + a.rec_words);
 
     const long item = (long)blockIdx.x * gpb + gi;
     if (item >= (long)a.pop * a.tiles) return;
     const int g = (int)(item / a.tiles);
     const int b0 = (int)(item - (long)g * a.tiles) * a.tile;
-    const int bt = min(a.tile, a.B - b0);
+    const int bt = T1 ? 1 : min(a.tile, a.B - b0);
 
-    // stage the record (independent of the previous kernel in the stream)
-    const uint4 *grec = reinterpret_cast<const uint4 *>(a.rec + (size_t)g * a.stride);
-    const uint4 h0 = ldg16(grec), h1 = ldg16(grec + 1);
-    const int n_nodes = (int)h0.x, n_levels = (int)h0.y;
-    const uint32_t status = h0.w;
-    const int words = min((int)(h1.x >> 4), a.rec_words);
-    for (int i = 2 + lane; i < words; i += G) srec[i] = ldg16(grec + i);
-
+    // 1. one bulk copy of the genome's record into shared memory; records do
+    //    not depend on the previous kernel in the stream, so this is issued
+    //    before the programmatic-dependence wait.
+    const uint8_t *grec = a.rec + (size_t)g * a.stride;
+    const uint32_t bar = smem_addr(bars + gi);
+    uint32_t bytes = (uint32_t)a.rec_copy_bytes;
+    if (bytes == 0) bytes = min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)),
+                                (uint32_t)a.rec_words * 16u);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(srec), grec, bytes, bar);
+    }
     if constexpr (PDL) {
         pdl_wait();
         pdl_trigger();
     }
+    // 2. this item's inputs, loaded into registers while the record is in flight
+    const int nx = bt * a.I;
+    const float *xb = a.x + ((size_t)g * a.B + b0) * a.I;
+    float xr[kInputRegs];
+#pragma unroll
+    for (int k = 0; k < kInputRegs; ++k) {
+        const int i = lane + k * G;
+        xr[k] = (i < nx) ? __ldg(xb + i) : 0.0f;
+    }
+    group_sync(G, gi);   // the mbarrier is initialised before anyone waits on it
     float *yb = a.y + ((size_t)g * a.B + b0) * a.O;
-    if (status & NEAT_G_ERROR_MASK) {
+    if (!mbar_wait(bar, 0)) {
+        atomicOr(&g_forward_error, kErrWaitExpired);
+        mbar_wait(bar, 0);                      // let the copy land before the block exits
         for (int i = lane; i < bt * a.O; i += G) yb[i] = __int_as_float(0x7fc00000);
         return;
     }
-    group_sync<G>(gi);
-
-    const int T = a.tile;
-    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
-    const float *xb = a.x + ((size_t)g * a.B + b0) * a.I;
-    for (int i = lane; i < bt * a.I; i += G) {
-        const int b = i / a.I, j = i - b * a.I;
-        v[io[j] * T + b] = __ldg(xb + i);
+    const uint4 h0 = srec[0], h1 = srec[1];
+    if (h0.z & NEAT_G_ERROR_MASK) {
+        for (int i = lane; i < bt * a.O; i += G) yb[i] = __int_as_float(0x7fc00000);
+        return;
     }
-    group_sync<G>(gi);
 
-    const uint4 *nodes = srec + 2;
-    const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
-    const int col = lane % T;
-    const int sub = lane / T;
-    const int nsub = G / T;
-    if (nsub == 1) {
-        if (col < bt)
-            for (int p = 0; p < n_nodes; ++p) eval_node(nodes[p], edges, v, p, T, col);
-    } else {
-        const uint16_t *lev = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.z);
-        for (int l = 0; l < n_levels; ++l) {
-            const int p1 = lev[l + 1];
-            if (col < bt)
-                for (int p = lev[l] + sub; p < p1; p += nsub) eval_node(nodes[p], edges, v, p, T, col);
-            group_sync<G>(gi);
+    // 3. inputs into the value tile v[position][tile]
+    const int lgT = T1 ? 0 : ilog2(a.tile);
+    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
+#pragma unroll
+    for (int k = 0; k < kInputRegs; ++k) {
+        const int i = lane + k * G;
+        if (i < nx) {
+            if (T1) v[io[i]] = xr[k];
+            else {
+                const int b = i / a.I, j = i - b * a.I;
+                v[((int)io[j] << lgT) + b] = xr[k];
+            }
         }
     }
-    group_sync<G>(gi);
+    for (int i = lane + kInputRegs * G; i < nx; i += G) {
+        if (T1) v[io[i]] = __ldg(xb + i);
+        else {
+            const int b = i / a.I, j = i - b * a.I;
+            v[((int)io[j] << lgT) + b] = __ldg(xb + i);
+        }
+    }
+    group_sync(G, gi);
+
+    // 4. node values level by level
+    if ((h0.w & 0xffffu) == kTraitsSumTanh)
+        walk_levels<T1, true>(srec, v, G, gi, lane, lgT, a.lg_split, T1 || (lane & (a.tile - 1)) < bt);
+    else
+        walk_levels<T1, false>(srec, v, G, gi, lane, lgT, a.lg_split, T1 || (lane & (a.tile - 1)) < bt);
+
+    // 5. outputs
     for (int i = lane; i < bt * a.O; i += G) {
-        const int b = i / a.O, j = i - b * a.O;
-        yb[i] = v[io[a.I + j] * T + b];
+        if (T1) yb[i] = v[io[a.I + i]];
+        else {
+            const int b = i / a.O, j = i - b * a.O;
+            yb[i] = v[((int)io[a.I + j] << lgT) + b];
+        }
     }
 }
 
 using KernelFn = void (*)(ForwardArgs);
 
-template <bool PDL>
-KernelFn pick(int G)
+KernelFn pick(bool pdl, bool t1)
 {
-    switch (G) {
-    case 2: return forward_kernel<2, PDL>;
-    case 4: return forward_kernel<4, PDL>;
-    case 8: return forward_kernel<8, PDL>;
-    case 16: return forward_kernel<16, PDL>;
-    case 32: return forward_kernel<32, PDL>;
-    case 64: return forward_kernel<64, PDL>;
-    case 128: return forward_kernel<128, PDL>;
-    case 256: return forward_kernel<256, PDL>;
-    case 512: return forward_kernel<512, PDL>;
-    }
-    return nullptr;
+    if (pdl) return t1 ? forward_kernel<true, true> : forward_kernel<true, false>;
+    return t1 ? forward_kernel<false, true> : forward_kernel<false, false>;
 }
 
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -178,13 +156,19 @@ int ensure_smem(KernelFn f, size_t bytes)
 
 }  // namespace
 
+// Records up to this size are copied whole (reserved size) in one bulk copy;
+// larger ones copy only their used bytes after reading the header.
+constexpr int kOnePieceRecordBytes = 8192;
+
 int check_launch(const neat_launch &L)
 {
-    if (!pow2(L.group) || L.group < 2 || L.group > 512) return invalid("launch: group must be a power of two in 2..512");
+    if (!pow2(L.group) || L.group > 1024) return invalid("launch: group must be a power of two in 1..1024");
     if (!pow2(L.tile) || L.tile > L.group) return invalid("launch: tile must be a power of two <= group");
     if (L.groups_per_block < 1 || L.group * L.groups_per_block > 1024)
         return invalid("launch: group * groups_per_block must be in 1..1024");
     if (L.group > 32 && L.groups_per_block > 15) return invalid("launch: at most 15 multi-warp groups per block");
+    if (L.split != 1 && L.split != 2 && L.split != 4) return invalid("launch: split must be 1, 2 or 4");
+    if (L.tile == 1 && L.split > L.group) return invalid("launch: split must not exceed group");
     return NEAT_OK;
 }
 
@@ -209,9 +193,12 @@ int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d, 
     a.N = d.max_nodes;
     a.B = batch;
     a.tile = L.tile;
+    a.group = L.group;
+    a.lg_split = L.split == 4 ? 2 : (L.split == 2 ? 1 : 0);
     a.tiles = (batch + L.tile - 1) / L.tile;
     a.rec_words = (int)(record_max_bytes(a.I, a.O, a.N, d.max_conns) / 16);
     a.val_floats = (a.N * L.tile + 3) & ~3;
+    a.rec_copy_bytes = (a.rec_words * 16 <= kOnePieceRecordBytes) ? a.rec_words * 16 : 0;
     *out = a;
     return NEAT_OK;
 }
@@ -221,10 +208,9 @@ int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s)
     const long items = (long)a.pop * a.tiles;
     if (items == 0) return NEAT_OK;
     const size_t per_group = (size_t)a.rec_words * 16 + (size_t)a.val_floats * 4;
-    const size_t smem = per_group * L.groups_per_block;
+    const size_t smem = per_group * L.groups_per_block + 16u * (size_t)((L.groups_per_block + 1) / 2);
     if (smem > 227 * 1024) return invalid("forward: shared memory per block exceeds 227 KB; lower tile or groups_per_block");
-    KernelFn f = L.pdl ? pick<true>(L.group) : pick<false>(L.group);
-    if (!f) return invalid("forward: unsupported group size");
+    KernelFn f = pick(L.pdl != 0, a.tile == 1);
     int rc = ensure_smem(f, smem);
     if (rc) return rc;
     const long grid = (items + L.groups_per_block - 1) / L.groups_per_block;
@@ -250,12 +236,82 @@ int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s)
 
 using namespace neat;
 
-extern "C" int neat_default_launch(neat_dims d, int32_t batch, neat_launch *out)
+namespace neat {
+namespace {
+
+struct DeviceCaps {
+    int sms = 152;
+    int smem_per_sm = 233472;
+};
+
+DeviceCaps device_caps()
+{
+    static std::mutex mu;
+    static std::unordered_map<int, DeviceCaps> cache;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DeviceCaps();
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    DeviceCaps c;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) c.sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0)
+        c.smem_per_sm = v;
+    cudaGetLastError();
+    cache[dev] = c;
+    return c;
+}
+
+// Groups per block: all items resident in as few waves as possible, with the
+// items spread evenly over the SMs (fewest groups on the busiest SM).
+int choose_groups_per_block(long items, int group, size_t per_group, const DeviceCaps &caps)
+{
+    const int max_gpb = group > 32 ? std::min(15, 1024 / group) : 1024 / group;
+    int best = 1;
+    long best_waves = -1, best_load = -1;
+    for (int gpb = 1; gpb <= max_gpb; ++gpb) {
+        const size_t smem = per_group * gpb + 16u * ((gpb + 1) / 2);
+        if (smem > 227u * 1024u) break;
+        const int threads = group * gpb;
+        const int warps = (threads + 31) / 32;
+        int resident = (int)(caps.smem_per_sm / (smem + 1024));
+        resident = std::min(resident, 2048 / (warps * 32));
+        resident = std::min(resident, 65536 / (warps * 32 * 64));
+        resident = std::min(resident, 32);
+        if (resident < 1) continue;
+        const long blocks = (items + gpb - 1) / gpb;
+        const long slots = (long)caps.sms * resident;
+        const long waves = (blocks + slots - 1) / slots;
+        const long load = ((blocks + caps.sms - 1) / caps.sms) * gpb;
+        // ties: the smallest block of at least 128 threads, so that blocks of
+        // the next launch can start (programmatic dependent launch) while the
+        // slowest blocks of this one finish
+        const bool smaller_ok = threads >= 128 || group * best < 128;
+        if (best_waves < 0 || waves < best_waves || (waves == best_waves && load < best_load) ||
+            (waves == best_waves && load == best_load && smaller_ok && group * best < 128)) {
+            best = gpb;
+            best_waves = waves;
+            best_load = load;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+}  // namespace neat
+
+extern "C" int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat_launch *out)
 {
     if (!out) return invalid("neat_default_launch: null pointer");
     if (!dims_ok(d)) return invalid("neat_default_launch: invalid dims");
+    if (pop < 0 || batch < 0) return invalid("neat_default_launch: pop and batch must be >= 0");
     neat_launch L;
     const int N = d.max_nodes;
+    L.split = 1;
     if (batch <= 1) {
         L.tile = 1;
         L.group = N <= 64 ? 8 : (N <= 256 ? 16 : 32);
@@ -268,11 +324,8 @@ extern "C" int neat_default_launch(neat_dims d, int32_t batch, neat_launch *out)
     }
     const size_t per_group = record_max_bytes(d.num_inputs, d.num_outputs, N, d.max_conns) +
                              4u * (size_t)((N * L.tile + 3) & ~3);
-    int gpb = 256 / L.group;
-    if (gpb < 1) gpb = 1;
-    while (gpb > 1 && per_group * gpb > 96 * 1024) gpb >>= 1;
-    if (L.group > 32 && gpb > 15) gpb = 8;
-    L.groups_per_block = gpb;
+    const long items = (long)std::max(pop, 1) * ((std::max(batch, 1) + L.tile - 1) / L.tile);
+    L.groups_per_block = choose_groups_per_block(items, L.group, per_group, device_caps());
     L.pdl = 0;
     *out = L;
     return NEAT_OK;
@@ -285,7 +338,7 @@ extern "C" int neat_forward_ex(const void *transformed_dev, int32_t pop, neat_di
     neat_launch L;
     if (launch_host) L = *launch_host;
     else {
-        int rc = neat_default_launch(d, batch, &L);
+        int rc = neat_default_launch(pop, d, batch, &L);
         if (rc) return rc;
     }
     ForwardArgs a;
@@ -324,7 +377,7 @@ static bool same_key(const neat_steps_cache &c, const void *rec, int32_t pop, co
            c.d.num_outputs == d.num_outputs && c.d.max_nodes == d.max_nodes && c.d.max_conns == d.max_conns &&
            c.x == x && c.xs == xs && c.batch == batch && c.y == y && c.ys == ys && c.steps == steps &&
            c.L.group == L.group && c.L.tile == L.tile && c.L.groups_per_block == L.groups_per_block &&
-           c.L.pdl == L.pdl;
+           c.L.pdl == L.pdl && c.L.split == L.split;
 }
 
 extern "C" int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_dims d, const float *inputs_dev,
@@ -339,7 +392,7 @@ extern "C" int neat_forward_steps(const void *transformed_dev, int32_t pop, neat
     neat_launch L;
     if (launch_host) L = *launch_host;
     else {
-        int rc = neat_default_launch(d, batch, &L);
+        int rc = neat_default_launch(pop, d, batch, &L);
         if (rc) return rc;
         L.pdl = 1;
     }
@@ -404,4 +457,20 @@ extern "C" void neat_steps_cache_destroy(neat_steps_cache *c)
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
+}
+
+extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
+{
+    clear_error();
+    if (!out_host) return invalid("neat_device_error: null pointer");
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_forward_error, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: read");
+    if (clear) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
+    }
+    *out_host = v;
+    return NEAT_OK;
 }

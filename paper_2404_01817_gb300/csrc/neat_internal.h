@@ -52,10 +52,13 @@ struct ForwardArgs {
     float *y;                // [pop][B][O]
     int pop, I, O, N;
     int B;                   // input vectors per genome
-    int tile;                // columns per work item
+    int group;               // threads per work item (power of two)
+    int tile;                // columns per work item (power of two)
+    int lg_split;            // log2 of threads per node when tile == 1
     int tiles;               // ceil(B / tile)
     int rec_words;           // 16-byte words of shared memory reserved for a record
     int val_floats;          // floats of shared memory for node values (N * tile, rounded to 4)
+    int rec_copy_bytes;      // bytes of each record copied in one piece (0: read the size from its header)
 };
 
 // Launch one forward over a single population (defined in neat_forward.cu).

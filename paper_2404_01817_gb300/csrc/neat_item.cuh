@@ -1,0 +1,198 @@
+// Evaluation of one work item from a genome record staged in shared memory:
+// the node rule of Section 3.3 applied level by level.  Shared by the
+// single-population forward kernel, the multi-population persistent kernel
+// and the CPPN query kernel.
+#pragma once
+
+#include "neat_device.cuh"
+#include "neat_internal.h"
+
+namespace neat {
+
+// Barrier among the G threads of group `gi` (G a power of two).  Groups of
+// at most a warp use a warp-level barrier on their lanes; larger groups use
+// a named barrier (id 1 + gi) unless the group is the whole block.
+__device__ __forceinline__ void group_sync(int G, int gi)
+{
+    if (G < 32) {
+        const unsigned base = (threadIdx.x & 31u) & ~(unsigned)(G - 1);
+        __syncwarp(((1u << G) - 1u) << base);
+    } else if (G == 32) {
+        __syncwarp();
+    } else if (G == (int)blockDim.x) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gi + 1), "r"(G) : "memory");
+    }
+}
+
+// Value slot of position p, column col.  T1: one column (tile 1).
+template <bool T1>
+__device__ __forceinline__ int vslot(uint32_t p, int lgT, int col)
+{
+    return T1 ? (int)p : (int)(p << lgT) + col;
+}
+
+// Aggregation order.  A node's incoming edges i = 0..ec-1 (record order) are
+// dealt round-robin into four partials, partial k = edges k, k+4, k+8, ...,
+// each accumulated in increasing i (sum and mean with fused multiply-add);
+// the aggregate is ((p0 . p1) . (p2 . p3)) with . the aggregation's binary
+// operation, divided by ec for the mean, and 0 when ec = 0.  The order is a
+// function of the genome alone: one thread, two or four threads per node
+// (combined through warp shuffles along the same tree) give identical bits.
+enum : uint32_t { kAggSum = 0, kAggProduct = 1, kAggMax = 2, kAggMean = 3 };
+
+__device__ __forceinline__ float agg_identity(uint32_t agg)
+{
+    // max starts from NaN: fmaxf(NaN, x) = x, and an all-NaN set stays NaN
+    return agg == kAggProduct ? 1.0f : (agg == kAggMax ? __int_as_float(0x7fc00000) : 0.0f);
+}
+
+__device__ __forceinline__ float agg_combine(uint32_t agg, float a, float b)
+{
+    return agg == kAggProduct ? a * b : (agg == kAggMax ? fmaxf(a, b) : a + b);
+}
+
+__device__ __forceinline__ float agg_step(uint32_t agg, float acc, float w, float x)
+{
+    return agg == kAggProduct ? acc * (w * x) : (agg == kAggMax ? fmaxf(acc, w * x) : fmaf(w, x, acc));
+}
+
+// Partials k0 .. k0+nk-1 of one node for one column, combined along the tree.
+template <bool T1, bool SUM>
+__device__ __forceinline__ float partials(uint32_t agg, const uint2 *__restrict__ e, uint32_t ec,
+                                          const float *__restrict__ v, int lgT, int col, int k0, int nk)
+{
+    if (SUM) agg = kAggSum;
+    const float id = SUM ? 0.0f : agg_identity(agg);
+    if (nk == 4) {
+        float q0 = id, q1 = id, q2 = id, q3 = id;
+        uint32_t i = 0;
+        for (; i + 4 <= ec; i += 4) {
+            const uint2 t0 = e[i], t1 = e[i + 1], t2 = e[i + 2], t3 = e[i + 3];
+            q0 = agg_step(agg, q0, __uint_as_float(t0.x), v[vslot<T1>(t0.y, lgT, col)]);
+            q1 = agg_step(agg, q1, __uint_as_float(t1.x), v[vslot<T1>(t1.y, lgT, col)]);
+            q2 = agg_step(agg, q2, __uint_as_float(t2.x), v[vslot<T1>(t2.y, lgT, col)]);
+            q3 = agg_step(agg, q3, __uint_as_float(t3.x), v[vslot<T1>(t3.y, lgT, col)]);
+        }
+        if (i < ec) { const uint2 t = e[i]; q0 = agg_step(agg, q0, __uint_as_float(t.x), v[vslot<T1>(t.y, lgT, col)]); }
+        if (i + 1 < ec) { const uint2 t = e[i + 1]; q1 = agg_step(agg, q1, __uint_as_float(t.x), v[vslot<T1>(t.y, lgT, col)]); }
+        if (i + 2 < ec) { const uint2 t = e[i + 2]; q2 = agg_step(agg, q2, __uint_as_float(t.x), v[vslot<T1>(t.y, lgT, col)]); }
+        return agg_combine(agg, agg_combine(agg, q0, q1), agg_combine(agg, q2, q3));
+    }
+    if (nk == 2) {
+        float q0 = id, q1 = id;
+        for (uint32_t i = (uint32_t)k0; i < ec; i += 4) {
+            const uint2 t0 = e[i];
+            q0 = agg_step(agg, q0, __uint_as_float(t0.x), v[vslot<T1>(t0.y, lgT, col)]);
+            if (i + 1 < ec) {
+                const uint2 t1 = e[i + 1];
+                q1 = agg_step(agg, q1, __uint_as_float(t1.x), v[vslot<T1>(t1.y, lgT, col)]);
+            }
+        }
+        return agg_combine(agg, q0, q1);
+    }
+    float q = id;
+    for (uint32_t i = (uint32_t)k0; i < ec; i += 4) {
+        const uint2 t = e[i];
+        q = agg_step(agg, q, __uint_as_float(t.x), v[vslot<T1>(t.y, lgT, col)]);
+    }
+    return q;
+}
+
+// Finish a node from its combined aggregate: mean division, empty set, node rule.
+__device__ __forceinline__ float node_output(const uint4 ne, uint32_t agg, uint32_t act, uint32_t ec, float a)
+{
+    if (agg == kAggMean) a = a / (float)ec;
+    if (ec == 0) a = 0.0f;
+    return activate(act, fmaf(__uint_as_float(ne.y), a, __uint_as_float(ne.x)));
+}
+
+// One whole node for one column (one thread): all four partials.
+template <bool T1, bool FAST>
+__device__ __forceinline__ void eval_node(const uint4 ne, const uint2 *__restrict__ edges,
+                                          float *__restrict__ v, int p, int lgT, int col)
+{
+    const uint32_t act = ne.w & 0xffu;
+    if (act == kInputAct) return;
+    const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
+    const uint32_t ec = ne.z >> 16;
+    const float a = partials<T1, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, lgT, col, 0, 4);
+    v[vslot<T1>(p, lgT, col)] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                                     : node_output(ne, agg, act, ec, a);
+}
+
+// All non-input nodes of a staged record, for the columns this thread owns.
+//  Columns (T > 1): thread `lane` = (sub, col) computes column col of nodes
+//  sub, sub + nsub, ... of every level, nsub = G / T.
+//  One column (T1): per level, `split` threads (1, 2 or 4, at most
+//  2^lg_split_max) share each node, lane = (slot, part); slots = G / split
+//  nodes of the level are in flight at once.
+// A group barrier separates levels.  Every thread of the group must call it.
+// FAST: every non-input node uses sum aggregation and tanh activation (the
+// setting of the paper's experiments), decoded once per genome.
+template <bool T1, bool FAST>
+__device__ __forceinline__ void walk_levels(const uint4 *srec, float *v, int G, int gi, int lane, int lgT,
+                                            int lg_split_max, bool col_ok)
+{
+    const uint4 h0 = srec[0], h1 = srec[1];
+    const int n_nodes = (int)(h0.x & 0xffffu), n_levels = (int)(h0.x >> 16);
+    const uint4 *nodes = srec + 2;
+    const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
+    const uint16_t *lev = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.z);
+    if (T1) {
+        // threads per node chosen per level: 4 when the level has at most
+        // G/4 nodes, 2 when at most G/2, else 1 (capped by lg_split_max);
+        // the leading input positions of level 0 are skipped
+        int p0 = (int)(h0.w >> 16);
+        for (int l = 0; l < n_levels; ++l) {
+            const int p1 = lev[l + 1];
+            const int cnt = p1 - p0;
+            const int lg_split = min(lg_split_max, (cnt * 4 <= G) ? 2 : ((cnt * 2 <= G) ? 1 : 0));
+            const int split = 1 << lg_split;
+            const int slot = lane >> lg_split, part = lane & (split - 1);
+            const int slots = G >> lg_split;
+            const int nk = 4 >> lg_split;
+            const unsigned mask = ((1u << split) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(split - 1));
+            for (int p = p0 + slot; p < p1; p += slots) {
+                const uint4 ne = nodes[p];
+                const uint32_t act = ne.w & 0xffu;
+                if (act == kInputAct) continue;              // same for every part of the slot
+                const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
+                const uint32_t ec = ne.z >> 16;
+                float a = partials<true, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, 0, 0, part * nk, nk);
+                for (int m = 1; m < split; m <<= 1) a = agg_combine(agg, a, __shfl_xor_sync(mask, a, m));
+                if (part == 0)
+                    v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                                : node_output(ne, agg, act, ec, a);
+            }
+            p0 = p1;
+            group_sync(G, gi);
+        }
+    } else {
+        const int col = lane & ((1 << lgT) - 1);
+        const int sub = lane >> lgT;
+        const int nsub = G >> lgT;
+        if (nsub == 1) {
+            if (col_ok)
+                for (int p = 0; p < n_nodes; ++p) eval_node<false, FAST>(nodes[p], edges, v, p, lgT, col);
+        } else {
+            int p0 = lev[0];
+            for (int l = 0; l < n_levels; ++l) {
+                const int p1 = lev[l + 1];
+                if (col_ok)
+                    for (int p = p0 + sub; p < p1; p += nsub) eval_node<false, FAST>(nodes[p], edges, v, p, lgT, col);
+                p0 = p1;
+                group_sync(G, gi);
+            }
+        }
+    }
+    group_sync(G, gi);
+}
+
+// Record traits word (header word 3): uniform activation | uniform aggregation << 8.
+constexpr uint32_t kTraitsSumTanh = 1u | (0u << 8);
+
+__device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
+
+}  // namespace neat

@@ -100,10 +100,12 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     short *src_row = reinterpret_cast<short *>(io_row + I + O);
     short *dst_row = src_row + C;
 
-    __shared__ unsigned int st;
+    __shared__ unsigned int st, acts_seen, aggs_seen;
     __shared__ int n_present, n_edges, max_level, changed;
     if (tid == 0) {
         st = 0;
+        acts_seen = 0;
+        aggs_seen = 0;
         n_present = 0;
         n_edges = 0;
         max_level = -1;
@@ -125,6 +127,10 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         const float bias = __ldg(nd + r * 5 + 1), resp = __ldg(nd + r * 5 + 2);
         const float agg = __ldg(nd + r * 5 + 3), act = __ldg(nd + r * 5 + 4);
         if (!is_enum(agg, 4) || !is_enum(act, 7)) lst |= NEAT_G_BADENUM;
+        else if (k >= (float)I) {
+            atomicOr(&acts_seen, 1u << (int)act);
+            atomicOr(&aggs_seen, 1u << (int)agg);
+        }
         if (isnan(bias) || isnan(resp)) lst |= NEAT_G_BADATTR;
         level[r] = -1;
         keymap[r] = ((unsigned long long)(uint32_t)k << 32) | (unsigned)r;
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     if (status & NEAT_G_ERROR_MASK) {
         if (tid == 0) {
             uint4 *h = reinterpret_cast<uint4 *>(rec);
-            h[0] = make_uint4((unsigned)n, 0u, 0u, status);
+            h[0] = make_uint4((unsigned)n, 0u, status, 0xffffu);
             h[1] = make_uint4(kHeaderBytes, kHeaderBytes, kHeaderBytes, kHeaderBytes);
             if (a.status) a.status[g] = status;
         }
@@ -267,11 +273,21 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
                                   (uint32_t)ebeg[p] | ((uint32_t)cnt[r] << 16),
                                   act | (agg << 8) | ((uint32_t)r << 16));
     }
+    // leading positions that are input nodes (a prefix of level 0)
+    __shared__ int lead_inputs;
+    if (tid == 0) lead_inputs = n;
+    __syncthreads();
+    for (int p = tid; p < n; p += nt)
+        if (__ldg(nd + (ordkey[p] & 0x7ffu) * 5) >= (float)I) atomicMin(&lead_inputs, p);
+    __syncthreads();
     uint16_t *io_out = reinterpret_cast<uint16_t *>(rec + off_io);
     for (int j = tid; j < I + O; j += nt) io_out[j] = (uint16_t)pos_of_row[io_row[j]];
     if (tid == 0) {
         uint4 *h = reinterpret_cast<uint4 *>(rec);
-        h[0] = make_uint4((unsigned)n, (unsigned)nl, (unsigned)E, status);
+        const uint32_t ua = __popc(acts_seen) == 1 ? (uint32_t)(__ffs(acts_seen) - 1) : 0xffu;
+        const uint32_t ug = __popc(aggs_seen) == 1 ? (uint32_t)(__ffs(aggs_seen) - 1) : 0xffu;
+        h[0] = make_uint4((unsigned)n | ((unsigned)nl << 16), (unsigned)E, status,
+                          ua | (ug << 8) | ((uint32_t)lead_inputs << 16));
         h[1] = make_uint4(used, off_edge, off_level, off_io);
         if (a.status) a.status[g] = status;
     }

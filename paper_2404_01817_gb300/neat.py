@@ -36,10 +36,14 @@ class Dims(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("groups_per_block", ctypes.c_int32), ("pdl", ctypes.c_int32)]
+                ("groups_per_block", ctypes.c_int32), ("pdl", ctypes.c_int32), ("split", ctypes.c_int32)]
+
+    def __init__(self, group=8, tile=1, groups_per_block=1, pdl=0, split=1):
+        super().__init__(group, tile, groups_per_block, pdl, split)
 
     def __repr__(self):
-        return f"Launch(group={self.group}, tile={self.tile}, groups_per_block={self.groups_per_block}, pdl={self.pdl})"
+        return (f"Launch(group={self.group}, tile={self.tile}, groups_per_block={self.groups_per_block}, "
+                f"pdl={self.pdl}, split={self.split})")
 
 
 _P = ctypes.c_void_p
@@ -51,7 +55,8 @@ _sig = {
     "neat_transformed_bytes": (ctypes.c_size_t, [_i32, Dims]),
     "neat_transform": (ctypes.c_int, [_P, _P, _i32, Dims, _P, ctypes.c_size_t, _P, _P]),
     "neat_forward": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, _P]),
-    "neat_default_launch": (ctypes.c_int, [Dims, _i32, ctypes.POINTER(Launch)]),
+    "neat_default_launch": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
+    "neat_device_error": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
@@ -107,10 +112,16 @@ def neat_transformed_bytes(pop: int, d: Dims) -> int:
     return _lib.neat_transformed_bytes(pop, d)
 
 
-def neat_default_launch(d: Dims, batch: int) -> Launch:
+def neat_default_launch(pop: int, d: Dims, batch: int) -> Launch:
     L = Launch()
-    _check(_lib.neat_default_launch(d, batch, ctypes.byref(L)), "neat_default_launch")
+    _check(_lib.neat_default_launch(pop, d, batch, ctypes.byref(L)), "neat_default_launch")
     return L
+
+
+def neat_device_error(clear: bool = True) -> int:
+    v = ctypes.c_uint32(0)
+    _check(_lib.neat_device_error(int(clear), ctypes.byref(v)), "neat_device_error")
+    return v.value
 
 
 def neat_transform(nodes, conns, d: Dims, transformed=None, status=None, stream=None):
@@ -197,6 +208,8 @@ class Decoded:
     in_w: np.ndarray         # [P][Cmax] float32 weights, 0 pad
     in_pos: np.ndarray       # [P][I]
     out_pos: np.ndarray      # [P][O]
+    uniform_activation: np.ndarray = None   # [P] id or 255
+    uniform_aggregation: np.ndarray = None  # [P] id or 255
 
 
 def decode_records(buf: np.ndarray, pop: int, d: Dims) -> Decoded:
@@ -206,15 +219,17 @@ def decode_records(buf: np.ndarray, pop: int, d: Dims) -> Decoded:
     N, C, I, O = d.max_nodes, d.max_conns, d.num_inputs, d.num_outputs
     buf = np.ascontiguousarray(buf[: stride * pop]).reshape(pop, stride)
     hdr = buf[:, :32].copy().view(np.uint32).reshape(pop, 8)
-    out = Decoded(n_nodes=hdr[:, 0].astype(np.int32), n_levels=hdr[:, 1].astype(np.int32),
-                  n_edges=hdr[:, 2].astype(np.int32), status=hdr[:, 3].copy(),
+    out = Decoded(n_nodes=(hdr[:, 0] & 0xFFFF).astype(np.int32), n_levels=(hdr[:, 0] >> 16).astype(np.int32),
+                  n_edges=hdr[:, 1].astype(np.int32), status=hdr[:, 2].copy(),
+                  uniform_activation=(hdr[:, 3] & 0xFF).astype(np.int32),
+                  uniform_aggregation=((hdr[:, 3] >> 8) & 0xFF).astype(np.int32),
                   order=np.full((pop, N), -1, np.int32), level_ptr=np.zeros((pop, N + 1), np.int32),
                   in_ptr=np.zeros((pop, N + 1), np.int32), in_src=np.full((pop, C), -1, np.int32),
                   in_w=np.zeros((pop, C), np.float32), in_pos=np.zeros((pop, I), np.int32),
                   out_pos=np.zeros((pop, O), np.int32))
     for g in range(pop):
-        n, nl, E = int(hdr[g, 0]), int(hdr[g, 1]), int(hdr[g, 2])
-        if hdr[g, 3] & G_ERROR_MASK:
+        n, nl, E = int(hdr[g, 0] & 0xFFFF), int(hdr[g, 0] >> 16), int(hdr[g, 1])
+        if hdr[g, 2] & G_ERROR_MASK:
             continue
         off_edge, off_level, off_io = int(hdr[g, 5]), int(hdr[g, 6]), int(hdr[g, 7])
         nodes = buf[g, 32:32 + 16 * n].copy()

@@ -51,7 +51,7 @@ def test_host_only_entry_points(lib_path):
     assert neat.neat_record_stride(neat.dims(1, 1, 4, 8193)) == 0          # too many conns
     for B in (1, 4, 64, 256):
         for N in (10, 50, 256, 1024):
-            L = neat.neat_default_launch(neat.dims(4, 2, N, 4 * N), B)
+            L = neat.neat_default_launch(1000, neat.dims(4, 2, N, 4 * N), B)
             assert L.group >= L.tile and L.group * L.groups_per_block <= 1024
 
 

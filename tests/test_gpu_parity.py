@@ -187,12 +187,18 @@ def test_forward_is_independent_of_launch_shape(neat):
         d, rec = _check_transform(neat, pop, "shape")
         x = _dev(W.normal_inputs(4, (pop.pop, B, pop.num_inputs)))
         outs = []
-        for group, tile, gpb in [(2, 1, 1), (8, 1, 16), (32, 1, 4), (32, 32, 2), (64, 8, 3), (256, 32, 1),
-                                 (16, 16, 8), (4, 4, 64)]:
+        for group, tile, gpb, split in [(2, 1, 1, 1), (8, 1, 16, 2), (32, 1, 4, 4), (4, 1, 32, 1), (16, 1, 8, 4),
+                                        (64, 1, 2, 2), (128, 1, 1, 1), (1, 1, 40, 1), (32, 32, 2, 1),
+                                        (64, 8, 3, 1), (256, 32, 1, 1), (16, 16, 8, 1), (4, 4, 64, 1),
+                                        (8, 8, 5, 1)]:
             if tile > 1 and B == 1:
                 continue
-            L = neat.Launch(group, tile, gpb, 0)
+            L = neat.Launch(group, tile, gpb, 0, split)
+            smem = gpb * (neat.neat_record_stride(d) + 4 * pop.max_nodes * tile)
+            if smem > 200 * 1024:
+                continue                      # beyond the shared memory of one block
             outs.append(neat.neat_forward(rec, pop.pop, d, x, launch=L).cpu().numpy())
+        assert len(outs) >= 4
         for o in outs[1:]:
             np.testing.assert_array_equal(o, outs[0])
         ref = oracle.forward(pop.nodes, pop.conns, pop.num_inputs, pop.num_outputs, x.cpu().numpy())
