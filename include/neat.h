@@ -245,12 +245,67 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
 
 /*
- * Device error word of the forward kernels: bit 0 is set when a bounded
- * on-device wait (the record copy into shared memory) ran out; the affected
- * outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
+ * Device error word of the forward and plan kernels: bit 0 is set when a
+ * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
+ * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).
  */
 NEAT_API int neat_device_error(int32_t clear, uint32_t *out_host);
+
+/* ------------------------------------------------------------ batching
+ *
+ * A plan evaluates several transformed populations -- of different
+ * dimensions and batch sizes -- with one persistent kernel launch per step.
+ * At creation the plan reads every record header once, splits each
+ * population into size buckets by node count (powers of two from 16, the
+ * bucket boundaries; or one bucket per population), picks a launch shape per
+ * bucket (heuristic, or timed on the plan's own data when `autotune` is set)
+ * and orders the buckets' work largest first.  Each step the persistent
+ * blocks pull work from a device counter, so uneven buckets balance across
+ * SMs.  Results are bit-identical to neat_forward on each population (the
+ * aggregation order is a function of the genome alone).
+ */
+typedef struct neat_pop_desc {
+    const void *transformed_dev;   /* records from neat_transform */
+    int32_t pop;
+    neat_dims dims;
+    int32_t batch;                 /* input vectors per genome per step */
+    const float *inputs_dev;       /* step s reads inputs_dev + s * in_step_stride: [pop][batch][I] */
+    int64_t in_step_stride;        /* floats */
+    float *outputs_dev;            /* step s writes outputs_dev + s * out_step_stride: [pop][batch][O] */
+    int64_t out_step_stride;       /* floats */
+} neat_pop_desc;
+
+typedef struct neat_plan_options {
+    int32_t autotune;       /* 1: time candidate shapes per bucket at creation (runs kernels on the plan's buffers) */
+    int32_t size_buckets;   /* 1: split populations by node count; 0: one bucket per population */
+    int32_t block_threads;  /* threads of a persistent block (0: 256) */
+    int32_t pdl;            /* 1: steps after the first use programmatic dependent launch */
+} neat_plan_options;
+
+typedef struct neat_plan neat_plan;
+
+/* Build a plan (synchronous on `stream`: reads headers, allocates its tables
+ * and work counters, optionally autotunes).  opt_host may be NULL (defaults:
+ * size buckets on, no autotune, 256 threads, pdl on).  Errors: NEAT_EINVAL,
+ * NEAT_ENOMEM, NEAT_ECUDA. */
+NEAT_API int neat_plan_create(const neat_pop_desc *pops_host, int32_t npops, const neat_plan_options *opt_host,
+                              void *stream, neat_plan **out_host);
+
+/* One step for every population of the plan (one kernel launch, plus a
+ * counter reset). */
+NEAT_API int neat_plan_forward(neat_plan *plan, int32_t step, void *stream);
+
+/* Steps first_step .. first_step+steps-1 as one CUDA graph (built on first
+ * use for these arguments, then replayed). */
+NEAT_API int neat_plan_forward_steps(neat_plan *plan, int32_t first_step, int32_t steps, void *stream);
+
+/* JSON description of the plan's buckets and launch shapes into buf (always
+ * NUL-terminated); returns the full length needed. */
+NEAT_API int neat_plan_describe(const neat_plan *plan, char *buf_host, int32_t len);
+
+/* Free the plan, its device tables and graphs (after its work completed). */
+NEAT_API void neat_plan_destroy(neat_plan *plan);
 
 /* Description of the last error on this thread ("" if none). */
 NEAT_API const char *neat_last_error(void);

@@ -45,6 +45,12 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Retire an mbarrier whose phases are complete before its memory is re-initialised.
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -58,18 +64,39 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Bounded wait for phase `phase` of `bar`; false if the bound ran out.
-constexpr uint32_t kWaitIters = 1u << 22;
-constexpr uint32_t kWaitHintNs = 2000;   // suspend up to this long per try instead of spinning
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `phase` of `bar`: false once about kWaitLimitNs of
+// wall time have passed without the phase completing.  Each try suspends
+// the thread for up to kWaitHintNs instead of spinning.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
+constexpr uint32_t kWaitHintNs = 2000;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
 {
-    for (uint32_t i = 0; i < kWaitIters; ++i) {
+    uint64_t t0 = 0;
+    for (uint32_t i = 0;; ++i) {
         uint32_t ok;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(bar), "r"(phase), "r"(kWaitHintNs) : "memory");
         if (ok) return true;
+        if ((i & 63u) == 0) {
+            const uint64_t t = global_ns();
+            if (i == 0) t0 = t;
+            else if (t - t0 > kWaitLimitNs) return false;
+        }
     }
-    return false;
+}
+
+// Order earlier generic-proxy accesses of shared memory before later
+// async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Bits of a translation unit's device error word.

@@ -27,8 +27,6 @@ namespace {
 // Library error word: a bounded wait in a forward kernel expired.
 __device__ unsigned int g_forward_error;
 
-constexpr int kInputRegs = 8;   // inputs prefetched into registers per thread
-
 // One work item per group of a.group threads.  T1: one input vector per
 // genome (tile 1), the case of a control loop that steps every genome once.
 template <bool PDL, bool T1>
@@ -39,9 +37,10 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
     const int gpb = blockDim.x >> lgG;
     const int gi = threadIdx.x >> lgG;
     const int lane = threadIdx.x & (G - 1);
-    // [mbarriers of the block's groups][group 0: record | values][group 1: ...]
+    // [mbarriers][flags][group 0: record | values][group 1: ...]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    uint4 *srec = smem + (gpb + 1) / 2 + (size_t)gi * (a.rec_words + a.val_floats / 4);
+    int *flags = reinterpret_cast<int *>(bars + gpb);
+    uint4 *srec = smem + forward_header_words(gpb) + (size_t)gi * (a.rec_words + a.val_floats / 4);
     float *v = reinterpret_cast<float *>(srec + a.rec_words);
 
     const long item = (long)blockIdx.x * gpb + gi;
@@ -50,15 +49,16 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
     const int b0 = (int)(item - (long)g * a.tiles) * a.tile;
     const int bt = T1 ? 1 : min(a.tile, a.B - b0);
 
-    // 1. one bulk copy of the genome's record into shared memory; records do
-    //    not depend on the previous kernel in the stream, so this is issued
-    //    before the programmatic-dependence wait.
+    // one bulk copy of the genome's record into shared memory; records do
+    // not depend on the previous kernel in the stream, so it is issued
+    // before the programmatic-dependence wait
     const uint8_t *grec = a.rec + (size_t)g * a.stride;
     const uint32_t bar = smem_addr(bars + gi);
     uint32_t bytes = (uint32_t)a.rec_copy_bytes;
     if (bytes == 0) bytes = min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)),
                                 (uint32_t)a.rec_words * 16u);
     if (lane == 0) {
+        flags[gi] = 0;
         mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, bytes);
         bulk_g2s(smem_addr(srec), grec, bytes, bar);
@@ -67,66 +67,8 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
         pdl_wait();
         pdl_trigger();
     }
-    // 2. this item's inputs, loaded into registers while the record is in flight
-    const int nx = bt * a.I;
-    const float *xb = a.x + ((size_t)g * a.B + b0) * a.I;
-    float xr[kInputRegs];
-#pragma unroll
-    for (int k = 0; k < kInputRegs; ++k) {
-        const int i = lane + k * G;
-        xr[k] = (i < nx) ? __ldg(xb + i) : 0.0f;
-    }
-    group_sync(G, gi);   // the mbarrier is initialised before anyone waits on it
-    float *yb = a.y + ((size_t)g * a.B + b0) * a.O;
-    if (!mbar_wait(bar, 0)) {
-        atomicOr(&g_forward_error, kErrWaitExpired);
-        mbar_wait(bar, 0);                      // let the copy land before the block exits
-        for (int i = lane; i < bt * a.O; i += G) yb[i] = __int_as_float(0x7fc00000);
-        return;
-    }
-    const uint4 h0 = srec[0], h1 = srec[1];
-    if (h0.z & NEAT_G_ERROR_MASK) {
-        for (int i = lane; i < bt * a.O; i += G) yb[i] = __int_as_float(0x7fc00000);
-        return;
-    }
-
-    // 3. inputs into the value tile v[position][tile]
-    const int lgT = T1 ? 0 : ilog2(a.tile);
-    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
-#pragma unroll
-    for (int k = 0; k < kInputRegs; ++k) {
-        const int i = lane + k * G;
-        if (i < nx) {
-            if (T1) v[io[i]] = xr[k];
-            else {
-                const int b = i / a.I, j = i - b * a.I;
-                v[((int)io[j] << lgT) + b] = xr[k];
-            }
-        }
-    }
-    for (int i = lane + kInputRegs * G; i < nx; i += G) {
-        if (T1) v[io[i]] = __ldg(xb + i);
-        else {
-            const int b = i / a.I, j = i - b * a.I;
-            v[((int)io[j] << lgT) + b] = __ldg(xb + i);
-        }
-    }
-    group_sync(G, gi);
-
-    // 4. node values level by level
-    if ((h0.w & 0xffffu) == kTraitsSumTanh)
-        walk_levels<T1, true>(srec, v, G, gi, lane, lgT, a.lg_split, T1 || (lane & (a.tile - 1)) < bt);
-    else
-        walk_levels<T1, false>(srec, v, G, gi, lane, lgT, a.lg_split, T1 || (lane & (a.tile - 1)) < bt);
-
-    // 5. outputs
-    for (int i = lane; i < bt * a.O; i += G) {
-        if (T1) yb[i] = v[io[a.I + i]];
-        else {
-            const int b = i / a.O, j = i - b * a.O;
-            yb[i] = v[((int)io[a.I + j] << lgT) + b];
-        }
-    }
+    run_item<T1>(srec, v, bar, flags + gi, G, gi, lane, a.x + ((size_t)g * a.B + b0) * a.I,
+                 a.y + ((size_t)g * a.B + b0) * a.O, a.I, a.O, bt, a.tile, a.lg_split, &g_forward_error);
 }
 
 using KernelFn = void (*)(ForwardArgs);
@@ -208,7 +150,7 @@ int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s)
     const long items = (long)a.pop * a.tiles;
     if (items == 0) return NEAT_OK;
     const size_t per_group = (size_t)a.rec_words * 16 + (size_t)a.val_floats * 4;
-    const size_t smem = per_group * L.groups_per_block + 16u * (size_t)((L.groups_per_block + 1) / 2);
+    const size_t smem = per_group * L.groups_per_block + 16u * (size_t)forward_header_words(L.groups_per_block);
     if (smem > 227 * 1024) return invalid("forward: shared memory per block exceeds 227 KB; lower tile or groups_per_block");
     KernelFn f = pick(L.pdl != 0, a.tile == 1);
     int rc = ensure_smem(f, smem);
@@ -274,7 +216,7 @@ int choose_groups_per_block(long items, int group, size_t per_group, const Devic
     int best = 1;
     long best_waves = -1, best_load = -1;
     for (int gpb = 1; gpb <= max_gpb; ++gpb) {
-        const size_t smem = per_group * gpb + 16u * ((gpb + 1) / 2);
+        const size_t smem = per_group * gpb + 16u * (size_t)forward_header_words(gpb);
         if (smem > 227u * 1024u) break;
         const int threads = group * gpb;
         const int warps = (threads + 31) / 32;
@@ -471,6 +413,9 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
         e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
         if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
     }
-    *out_host = v;
+    unsigned int vp = 0;
+    int rc = read_plan_error(&vp, clear);
+    if (rc) return rc;
+    *out_host = v | vp;
     return NEAT_OK;
 }

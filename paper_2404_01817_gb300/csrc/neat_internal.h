@@ -61,11 +61,16 @@ struct ForwardArgs {
     int rec_copy_bytes;      // bytes of each record copied in one piece (0: read the size from its header)
 };
 
+// 16-byte words before the groups' regions in a forward block's shared
+// memory: one mbarrier (8 B) and one flag (4 B) per group.
+__host__ __device__ inline int forward_header_words(int groups) { return (groups * 12 + 15) / 16; }
+
 // Launch one forward over a single population (defined in neat_forward.cu).
 int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s);
 int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d,
                       const float *inputs, int32_t batch, float *outputs,
                       const neat_launch &L, ForwardArgs *out);
 int check_launch(const neat_launch &L);
+int read_plan_error(unsigned int *v, int clear);   // neat_plan.cu
 
 }  // namespace neat

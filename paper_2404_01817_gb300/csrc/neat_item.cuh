@@ -195,4 +195,72 @@ constexpr uint32_t kTraitsSumTanh = 1u | (0u << 8);
 
 __device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
 
+constexpr int kInputRegs = 8;   // inputs prefetched into registers per thread
+
+// Everything of one work item after its record copy was issued by lane 0
+// (mbarrier `bar` initialised and armed, `flag` set to 0, both before the
+// call): inputs are read into registers while the copy is in flight, the
+// group waits for the record (a bounded wait; on expiry the device error
+// word gets kErrWaitExpired and the outputs NaN), scatters the inputs into
+// the value tile, walks the levels and writes the outputs.
+//   xb: inputs of the item [bt][I]; yb: its outputs [bt][O].
+template <bool T1>
+__device__ __forceinline__ void run_item(const uint4 *srec, float *v, uint32_t bar, volatile int *flag, int G,
+                                         int gi, int lane, const float *__restrict__ xb, float *__restrict__ yb,
+                                         int I, int O, int bt, int tile, int lg_split, unsigned int *err)
+{
+    const int lgT = T1 ? 0 : ilog2(tile);
+    const int nx = bt * I;
+    float xr[kInputRegs];
+#pragma unroll
+    for (int k = 0; k < kInputRegs; ++k) {
+        const int i = lane + k * G;
+        xr[k] = (i < nx) ? __ldg(xb + i) : 0.0f;
+    }
+    group_sync(G, gi);                    // barrier initialised before anyone waits on it
+    if (!mbar_wait(bar, 0)) *flag = 1;
+    group_sync(G, gi);
+    if (*flag) {                          // uniform over the group
+        if (lane == 0) atomicOr(err, kErrWaitExpired);
+        mbar_wait(bar, 0);                // let the copy land before the region is reused
+        for (int i = lane; i < bt * O; i += G) yb[i] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const uint4 h0 = srec[0], h1 = srec[1];
+    if (h0.z & NEAT_G_ERROR_MASK) {
+        for (int i = lane; i < bt * O; i += G) yb[i] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
+#pragma unroll
+    for (int k = 0; k < kInputRegs; ++k) {
+        const int i = lane + k * G;
+        if (i < nx) {
+            if (T1) v[io[i]] = xr[k];
+            else {
+                const int b = i / I, j = i - b * I;
+                v[((int)io[j] << lgT) + b] = xr[k];
+            }
+        }
+    }
+    for (int i = lane + kInputRegs * G; i < nx; i += G) {
+        if (T1) v[io[i]] = __ldg(xb + i);
+        else {
+            const int b = i / I, j = i - b * I;
+            v[((int)io[j] << lgT) + b] = __ldg(xb + i);
+        }
+    }
+    group_sync(G, gi);
+    const bool col_ok = T1 || (lane & (tile - 1)) < bt;
+    if ((h0.w & 0xffffu) == kTraitsSumTanh) walk_levels<T1, true>(srec, v, G, gi, lane, lgT, lg_split, col_ok);
+    else walk_levels<T1, false>(srec, v, G, gi, lane, lgT, lg_split, col_ok);
+    for (int i = lane; i < bt * O; i += G) {
+        if (T1) yb[i] = v[io[I + i]];
+        else {
+            const int b = i / O, j = i - b * O;
+            yb[i] = v[((int)io[I + j] << lgT) + b];
+        }
+    }
+}
+
 }  // namespace neat

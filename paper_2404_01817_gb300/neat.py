@@ -50,6 +50,15 @@ _P = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
 
+
+class PopDesc(ctypes.Structure):
+    _fields_ = [("transformed", _P), ("pop", _i32), ("dims", Dims), ("batch", _i32),
+                ("inputs", _P), ("in_step_stride", _i64), ("outputs", _P), ("out_step_stride", _i64)]
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("autotune", _i32), ("size_buckets", _i32), ("block_threads", _i32), ("pdl", _i32)]
+
 _sig = {
     "neat_record_stride": (ctypes.c_size_t, [Dims]),
     "neat_transformed_bytes": (ctypes.c_size_t, [_i32, Dims]),
@@ -61,6 +70,12 @@ _sig = {
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
     "neat_steps_cache_destroy": (None, [_P]),
+    "neat_plan_create": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, ctypes.POINTER(PlanOptions), _P,
+                                        ctypes.POINTER(_P)]),
+    "neat_plan_forward": (ctypes.c_int, [_P, _i32, _P]),
+    "neat_plan_forward_steps": (ctypes.c_int, [_P, _i32, _i32, _P]),
+    "neat_plan_describe": (ctypes.c_int, [_P, ctypes.c_char_p, _i32]),
+    "neat_plan_destroy": (None, [_P]),
     "neat_last_error": (ctypes.c_char_p, []),
     "neat_version": (ctypes.c_char_p, []),
 }
@@ -190,6 +205,57 @@ def neat_forward_steps(transformed, pop: int, d: Dims, inputs, outputs, cache: S
                                    ctypes.byref(cache.handle), _stream(stream))
     _check(code, "neat_forward_steps")
     return outputs
+
+
+class Plan:
+    """neat_plan_*: several transformed populations, one persistent launch per step.
+
+    pops: sequence of dicts with keys transformed, pop, dims, inputs, outputs
+    (torch CUDA tensors; inputs [S][pop][batch][I] or [pop][batch][I],
+    outputs likewise), the step strides being taken from the leading
+    dimension when the tensors are 4-D."""
+
+    def __init__(self, pops, autotune: bool = False, size_buckets: bool = True, block_threads: int = 0,
+                 pdl: bool = True, stream=None):
+        descs = (PopDesc * len(pops))()
+        self._keep = []
+        for i, p in enumerate(pops):
+            x, y = p["inputs"], p["outputs"]
+            batch = x.shape[-2]
+            d = p["dims"]
+            in_step = x.shape[-3] * batch * d.num_inputs if x.dim() == 4 else 0
+            out_step = y.shape[-3] * batch * d.num_outputs if y.dim() == 4 else 0
+            descs[i] = PopDesc(_ptr(p["transformed"]), p["pop"], d, batch, _ptr(x), in_step, _ptr(y), out_step)
+            self._keep.append((p["transformed"], x, y))
+        opt = PlanOptions(int(autotune), int(size_buckets), block_threads, int(pdl))
+        self.handle = _P(None)
+        _check(_lib.neat_plan_create(descs, len(pops), ctypes.byref(opt), _stream(stream), ctypes.byref(self.handle)),
+               "neat_plan_create")
+
+    def forward(self, step: int = 0, stream=None):
+        _check(_lib.neat_plan_forward(self.handle, step, _stream(stream)), "neat_plan_forward")
+
+    def forward_steps(self, first_step: int, steps: int, stream=None):
+        _check(_lib.neat_plan_forward_steps(self.handle, first_step, steps, _stream(stream)),
+               "neat_plan_forward_steps")
+
+    def describe(self) -> dict:
+        import json
+        n = _lib.neat_plan_describe(self.handle, None, 0)
+        buf = ctypes.create_string_buffer(n)
+        _lib.neat_plan_describe(self.handle, buf, n)
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if self.handle.value:
+            _lib.neat_plan_destroy(self.handle)
+            self.handle = _P(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------- record decoding
