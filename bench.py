@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
+    ap.add_argument("--workload", choices=["ant", "batched", "cppn"], default="ant",
+                    help="ant: the headline line; batched / cppn: the uneven-batch and CPPN shapes")
     return ap.parse_args()
 
 
@@ -185,10 +187,117 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_events(fn, reps, stream):
+    """Run fn reps times between CUDA events on `stream`; per-rep ms."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_batched(args):
+    """Uneven batch: 4 populations x 2048 genomes (max nodes 16/64/256/1024,
+    conns ~4x nodes, all activations and aggregations), 64 N(0,1) inputs per
+    genome per step, 100 steps; the plan (one persistent launch per step, as
+    a CUDA graph) against plain per-population launches."""
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    S, B = 100, 64
+    pops = W.batched_populations(0, pop=2048)
+    descs = []
+    for j, p in enumerate(pops):
+        d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
+        rec, st = neat.neat_transform(torch.from_numpy(p.nodes).to(dev), torch.from_numpy(p.conns).to(dev), d)
+        g = torch.Generator(device=dev)
+        g.manual_seed(10 + j)
+        x = torch.randn((S, p.pop, B, p.num_inputs), device=dev, generator=g)
+        y = torch.empty((S, p.pop, B, p.num_outputs), device=dev)
+        descs.append(dict(transformed=rec, pop=p.pop, dims=d, inputs=x, outputs=y))
+    stream = torch.cuda.current_stream(dev)
+    plan = neat.Plan(descs, autotune=True)
+    for _ in range(args.warmup):
+        plan.forward_steps(0, S)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ms_b = timed_events(lambda: plan.forward_steps(0, S), args.steps, stream)
+    launches = [neat.neat_default_launch(p.pop, dd["dims"], B) for p, dd in zip(pops, descs)]
+
+    def plain():
+        for s in range(S):
+            for p, dd, L in zip(pops, descs, launches):
+                neat.neat_forward(dd["transformed"], p.pop, dd["dims"], dd["inputs"][s], dd["outputs"][s],
+                                  launch=L, stream=stream)
+    plain()
+    ms_p = timed_events(plain, max(1, min(args.steps, 5)), stream)
+    gf = sum(p.pop for p in pops) * B * S
+    line = {"metric": "genome-forwards/s (batched uneven: 4 pops x 2048, Nmax 16/64/256/1024, B=64)",
+            "value": gf / (statistics.median(ms_b) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.median(ms_b) / S, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched uneven", "steps_per_graph": S, "batch": B},
+            "plain": {"value": gf / (statistics.median(ms_p) / 1e3), "ms_per_step": statistics.median(ms_p) / S},
+            "plan": plan.describe(), "clocks": clocks.summary(),
+            "gpu_launches": args.steps * S}
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_cppn(args):
+    """CPPN substrate batch: 1000 CPPNs x 131072 queries (3 layers of 16x16)."""
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    pop = W.cppn_population(0, 1000)
+    d = neat.dims(5, 1, pop.max_nodes, pop.max_conns)
+    nodes = torch.from_numpy(pop.nodes).to(dev)
+    conns = torch.from_numpy(pop.conns).to(dev)
+    rec, st = neat.neat_transform(nodes, conns, d)
+    w = torch.empty((1000, 2, 256, 256), device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        neat.neat_transform(nodes, conns, d, rec, st, stream=stream)
+        neat.neat_cppn_query(rec, 1000, d, 16, 3, 0.2, w, stream=stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ms = timed_events(step, args.steps, stream)
+    hdr = rec.view(1000, -1)[:, :32].cpu().numpy().view(np.uint32)
+    edges = hdr[:, 1].astype(np.int64)
+    nonin = (hdr[:, 0] & 0xFFFF).astype(np.int64) - 5
+    q = 1000 * 131072
+    t = statistics.median(ms) / 1e3
+    flops = 131072 * int((2 * edges + 2 * nonin).sum())       # one FMA per edge, bias/response FMA per node
+    sm_mhz = clocks.summary()["sm_mhz"] or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12            # TFLOP/s at the sampled clock
+    line = {"metric": "CPPN substrate queries/s (1000 CPPNs x 131072 queries, 3 layers of 16x16)",
+            "value": q / t, "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(ms), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / fp32_peak,
+                         "note": "FMA flops of the edges and node rule only; transcendental work excluded"},
+            "clocks": clocks.summary(), "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "cppn":
+        run_cppn(args)
         return
     import torch
     rank, local_rank, world = dist_env()

@@ -245,12 +245,33 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
 
 /*
- * Device error word of the forward and plan kernels: bit 0 is set when a
+ * Device error word of the forward, plan and CPPN kernels: bit 0 is set when a
  * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
  * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).
  */
 NEAT_API int neat_device_error(int32_t clear, uint32_t *out_host);
+
+/* ---------------------------------------------------------- CPPN query
+ *
+ * CPPN / HyperNEAT extension (Section 4.3): each genome is a CPPN with the
+ * five inputs (x_s, y_s, x_t, y_t, 1) and one output, queried at every pair
+ * (source node of layer l, target node of layer l+1) of a substrate of
+ * `layers` layers, each a res x res grid over [-1,1]^2 with coordinate
+ * -1 + 2 i / (res - 1) (computed in double, rounded to float) and node index
+ * res * iy + ix.  The weight is the CPPN output, set to 0 when
+ * |w| < threshold (the comparison made in float32).
+ */
+typedef struct neat_substrate {
+    int32_t resolution;   /* nodes per side of a layer, 2..181 */
+    int32_t layers;       /* >= 2 */
+} neat_substrate;
+
+/* weights_dev: f32 [pop][layers-1][res*res][res*res] (written; NaN for
+ * genomes with an error bit).  d must have num_inputs = 5, num_outputs = 1
+ * and max_nodes <= 160.  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_dims d, neat_substrate sub,
+                             float threshold, float *weights_dev, void *stream);
 
 /* ------------------------------------------------------------ batching
  *

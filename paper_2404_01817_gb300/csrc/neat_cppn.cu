@@ -1,0 +1,164 @@
+// CPPN query of a HyperNEAT substrate (the CPPN / HyperNEAT extensions of
+// Section 4.3): every CPPN genome is evaluated at every (source, target) node
+// pair of consecutive substrate layers, with inputs (x_s, y_s, x_t, y_t, 1),
+// and its output becomes the connection weight, zeroed when |w| < threshold.
+//
+// Substrate: `layers` layers of res x res nodes on the grid -1 + 2 i / (res-1)
+// of [-1,1]^2, node index = res * iy + ix.  Output layout
+// weights[genome][block][source][target], block l joining layer l to l+1.
+//
+// GB300 mapping: a block of 256 threads takes (genome, chunk of queries),
+// bulk-copies the genome's record into shared memory once (TMA + mbarrier),
+// and each thread evaluates its own queries one after another in its own
+// column of the value tile v[position][256]: node and edge reads are the same
+// for the whole warp (broadcasts), value reads hit 32 distinct banks, and no
+// barrier is needed between nodes.  The work is bound by FP32 and SFU issue
+// (edges and transcendentals per query), not by memory: the only traffic is
+// the 4-byte output per query.
+#include "neat_device.cuh"
+#include "neat_internal.h"
+#include "neat_item.cuh"
+
+namespace neat {
+namespace {
+
+constexpr int kCppnThreads = 256;
+constexpr int kCppnQueriesPerThread = 16;
+
+struct CppnArgs {
+    const uint8_t *rec;
+    size_t stride;
+    float *out;
+    int pop, N;
+    int res, layers;
+    long queries;            // per genome
+    int chunks;              // blocks per genome
+    float threshold;
+    int rec_words;           // 16-byte words of the record region
+};
+
+__device__ unsigned int g_cppn_error;
+
+__global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
+{
+    extern __shared__ __align__(16) uint4 smem[];
+    __shared__ uint64_t bar_mem;
+    __shared__ float coord[NEAT_MAX_NODES];
+    const int tid = threadIdx.x;
+    const int g = (int)(blockIdx.x / a.chunks);
+    const long q0 = (long)(blockIdx.x - (long)g * a.chunks) * (kCppnThreads * kCppnQueriesPerThread);
+    uint4 *srec = smem;
+    float *v = reinterpret_cast<float *>(smem + a.rec_words);
+    const uint32_t bar = smem_addr(&bar_mem);
+    const uint8_t *grec = a.rec + (size_t)g * a.stride;
+    if (tid == 0) {
+        const uint32_t bytes = min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)),
+                                   (uint32_t)a.rec_words * 16u);
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(srec), grec, bytes, bar);
+    }
+    for (int i = tid; i < a.res; i += kCppnThreads)
+        coord[i] = (float)(-1.0 + 2.0 * (double)i / (double)(a.res - 1));
+    __syncthreads();
+    __shared__ int failed;
+    if (tid == 0) failed = 0;
+    __syncthreads();
+    if (!mbar_wait(bar, 0)) failed = 1;
+    __syncthreads();
+    float *out = a.out + (size_t)g * a.queries;
+    const long qend = min(a.queries, q0 + (long)kCppnThreads * kCppnQueriesPerThread);
+    if (failed) {
+        if (tid == 0) atomicOr(&g_cppn_error, kErrWaitExpired);
+        mbar_wait(bar, 0);
+        for (long q = q0 + tid; q < qend; q += kCppnThreads) out[q] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const uint4 h0 = srec[0], h1 = srec[1];
+    if (h0.z & NEAT_G_ERROR_MASK) {
+        for (long q = q0 + tid; q < qend; q += kCppnThreads) out[q] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int n_nodes = (int)(h0.x & 0xffffu);
+    const int first = (int)(h0.w >> 16);               // leading input positions need no evaluation
+    const uint4 *nodes = srec + 2;
+    const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
+    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
+    const int lgT = ilog2(kCppnThreads);
+    const int pin0 = io[0], pin1 = io[1], pin2 = io[2], pin3 = io[3], pin4 = io[4], pout = io[5];
+    const long per_block = (long)a.res * a.res * a.res * a.res;
+    const int rr = a.res * a.res;
+    for (long q = q0 + tid; q < qend; q += kCppnThreads) {
+        const int r = (int)(q % per_block);
+        const int s = r / rr, t = r - s * rr;
+        v[(pin0 << lgT) + tid] = coord[s % a.res];
+        v[(pin1 << lgT) + tid] = coord[s / a.res];
+        v[(pin2 << lgT) + tid] = coord[t % a.res];
+        v[(pin3 << lgT) + tid] = coord[t / a.res];
+        v[(pin4 << lgT) + tid] = 1.0f;
+        for (int p = first; p < n_nodes; ++p) eval_node<false, false>(nodes[p], edges, v, p, lgT, tid);
+        const float w = v[(pout << lgT) + tid];
+        out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
+    }
+}
+
+}  // namespace
+}  // namespace neat
+
+using namespace neat;
+
+extern "C" int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_dims d, neat_substrate sub,
+                               float threshold, float *weights_dev, void *stream)
+{
+    clear_error();
+    if (!dims_ok(d)) return invalid("neat_cppn_query: invalid dims");
+    if (d.num_inputs != 5 || d.num_outputs != 1)
+        return invalid("neat_cppn_query: a CPPN has 5 inputs (x_s, y_s, x_t, y_t, 1) and 1 output");
+    if (sub.resolution < 2 || sub.resolution > 181 || sub.layers < 2)
+        return invalid("neat_cppn_query: substrate resolution must be in 2..181 and layers >= 2");
+    if (pop < 0) return invalid("neat_cppn_query: pop < 0");
+    if (pop == 0) return NEAT_OK;
+    if (!transformed_dev || !weights_dev) return invalid("neat_cppn_query: null pointer");
+    if (reinterpret_cast<uintptr_t>(transformed_dev) & 15u)
+        return invalid("neat_cppn_query: transformed must be 16-byte aligned");
+    CppnArgs a;
+    a.rec = static_cast<const uint8_t *>(transformed_dev);
+    a.stride = record_stride(d);
+    a.out = weights_dev;
+    a.pop = pop;
+    a.N = d.max_nodes;
+    a.res = sub.resolution;
+    a.layers = sub.layers;
+    const long r2 = (long)sub.resolution * sub.resolution;
+    a.queries = (long)(sub.layers - 1) * r2 * r2;
+    const long per_block = (long)kCppnThreads * kCppnQueriesPerThread;
+    a.chunks = (int)((a.queries + per_block - 1) / per_block);
+    a.threshold = threshold;
+    a.rec_words = (int)(record_max_bytes(5, 1, d.max_nodes, d.max_conns) / 16);
+    const size_t smem = (size_t)a.rec_words * 16 + 4u * (size_t)d.max_nodes * kCppnThreads;
+    if (smem > 200u * 1024u) return invalid("neat_cppn_query: genome too large for one block (max_nodes <= 160)");
+    const long blocks = (long)pop * a.chunks;
+    if (blocks > 0x7fffffffL) return invalid("neat_cppn_query: too many queries");
+    if (smem > 48u * 1024u) {
+        cudaError_t e = cudaFuncSetAttribute(cppn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "neat_cppn_query: cudaFuncSetAttribute");
+    }
+    cppn_kernel<<<(unsigned)blocks, kCppnThreads, smem, as_stream(stream)>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_cppn_query: launch");
+    return NEAT_OK;
+}
+
+namespace neat {
+int read_cppn_error(unsigned int *v, int clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_cppn_error, sizeof(*v));
+    if (e != cudaSuccess) return cuda_fail(e, "cppn error word: read");
+    if (clear) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_cppn_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_fail(e, "cppn error word: clear");
+    }
+    return NEAT_OK;
+}
+}  // namespace neat

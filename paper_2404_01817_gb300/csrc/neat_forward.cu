@@ -413,9 +413,10 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
         e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
         if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
     }
-    unsigned int vp = 0;
+    unsigned int vp = 0, vc = 0;
     int rc = read_plan_error(&vp, clear);
+    if (rc == NEAT_OK) rc = read_cppn_error(&vc, clear);
     if (rc) return rc;
-    *out_host = v | vp;
+    *out_host = v | vp | vc;
     return NEAT_OK;
 }

@@ -72,5 +72,6 @@ int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d,
                       const neat_launch &L, ForwardArgs *out);
 int check_launch(const neat_launch &L);
 int read_plan_error(unsigned int *v, int clear);   // neat_plan.cu
+int read_cppn_error(unsigned int *v, int clear);   // neat_cppn.cu
 
 }  // namespace neat

@@ -166,6 +166,8 @@ struct neat_plan {
     cudaGraphExec_t exec = nullptr;
     int graph_first = -1, graph_steps = -1;
     std::string autotune_log;
+    int max_footprint_bucket = -1;    // host bucket whose groups take the most shared memory
+    size_t smem_override = 0;         // while timing one bucket: its own footprint
 };
 
 namespace neat {
@@ -241,6 +243,17 @@ int layout(neat_plan *P, cudaStream_t s)
     P->bd = bd;
     P->total_items = cta;
     P->smem = smem_regions + 16u * forward_header_words(NT);
+    P->max_footprint_bucket = -1;
+    {
+        size_t best = 0;
+        for (size_t i = 0; i < bd.size(); ++i) {
+            const size_t f = (size_t)bd[i].region_words * 16 * bd[i].gpc;
+            if (f > best) {
+                best = f;
+                P->max_footprint_bucket = order[i];
+            }
+        }
+    }
     if (P->d_buckets) cudaFree(P->d_buckets);
     cudaError_t e = cudaMalloc(&P->d_buckets, sizeof(BucketDev) * std::max<size_t>(bd.size(), 1));
     if (e != cudaSuccess) return cuda_fail(e, "plan: cudaMalloc buckets");
@@ -287,7 +300,7 @@ int launch_step(neat_plan *P, int lo, int hi, unsigned int *ctr, int step, bool 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::max(1, std::min(P->grid, hi - lo)));
     cfg.blockDim = dim3((unsigned)P->block_threads);
-    cfg.dynamicSmemBytes = P->smem;
+    cfg.dynamicSmemBytes = P->smem_override ? P->smem_override : P->smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     if (pdl) {
@@ -308,6 +321,17 @@ int launch_step(neat_plan *P, int lo, int hi, unsigned int *ctr, int step, bool 
 float time_bucket(neat_plan *P, int bi, cudaStream_t s, int reps)
 {
     const BucketDev &d = P->bd[bi];
+    P->smem_override = (size_t)d.region_words * 16 * d.gpc + 16u * forward_header_words(P->block_threads);
+    const int grid_saved = P->grid;
+    {
+        int dev = 0, sms = 152, smem_sm = 233472;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        int per_sm = (int)(smem_sm / (P->smem_override + 1024));
+        per_sm = std::max(1, std::min(per_sm, 2048 / P->block_threads));
+        P->grid = sms * per_sm;
+    }
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -327,6 +351,30 @@ float time_bucket(neat_plan *P, int bi, cudaStream_t s, int reps)
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    P->smem_override = 0;
+    P->grid = grid_saved;
+    return best;
+}
+
+// Time one whole step of the laid-out plan (best of reps).
+float time_plan(neat_plan *P, cudaStream_t s, int reps)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int r = 0; r < reps + 1; ++r) {
+        cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned int), s);
+        cudaEventRecord(a, s);
+        if (launch_step(P, 0, P->total_items, P->d_counters, 0, false, s) != NEAT_OK) break;
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     return best;
 }
 
@@ -338,45 +386,96 @@ std::vector<Shape> candidates(int n_class, int batch, int NT)
             for (int split : {1, 2})
                 if (G <= NT) c.push_back(Shape{G, 1, split});
     } else {
-        for (int t : {8, 16, 32})
-            for (int nsub : {1, 2, 4, 8}) {
-                if (t > 2 * batch && t > 8) continue;
-                if (t * nsub <= NT && (nsub == 1 || n_class > 16)) c.push_back(Shape{t * nsub, t, 1});
+        for (int t : {4, 8, 16, 32}) {
+            if (t > 2 * batch && t > 4) continue;
+            for (int nsub : {1, 2, 4, 8, 16, 32}) {
+                if (t * nsub > NT || t * nsub < 8) continue;
+                if (nsub > 1 && nsub * 4 > n_class) continue;       // more threads than a level can use
+                c.push_back(Shape{t * nsub, t, 1});
             }
+        }
     }
     return c;
+}
+
+// Footprint in shared memory of a bucket's groups in one block.
+size_t footprint(const neat_plan *P, const HostBucket &h)
+{
+    int gpc = P->block_threads / h.shape.G;
+    if (h.shape.G > 32) gpc = std::min(gpc, 15);
+    return region_bytes(h, 0, 0) * gpc;
 }
 
 int autotune(neat_plan *P, cudaStream_t s)
 {
     char line[256];
+    auto position_of = [&](size_t hbi) {
+        size_t goff = 0;
+        for (size_t i = 0; i < hbi; ++i) goff += P->hb[i].gidx.size();
+        for (size_t i = 0; i < P->bd.size(); ++i)
+            if (P->bd[i].gidx == P->d_gidx + goff) return (int)i;
+        return -1;
+    };
+    // 1. each bucket alone, at its own shared-memory footprint
+    std::vector<std::vector<std::pair<float, Shape>>> timed(P->hb.size());
     for (size_t hbi = 0; hbi < P->hb.size(); ++hbi) {
         HostBucket &h = P->hb[hbi];
         const neat_pop_desc &pd = P->pops[h.pop_index];
-        Shape best = h.shape;
-        float best_ms = 1e30f;
+        const Shape keep = h.shape;
         for (const Shape &c : candidates(h.n_class, pd.batch, P->block_threads)) {
             h.shape = c;
-            if (layout(P, s) != NEAT_OK) continue;
-            // this bucket's position in the laid-out table
-            int pos = -1;
-            size_t goff = 0;
-            for (size_t i = 0; i < hbi; ++i) goff += P->hb[i].gidx.size();
-            for (size_t i = 0; i < P->bd.size(); ++i)
-                if (P->bd[i].gidx == P->d_gidx + goff) pos = (int)i;
-            if (pos < 0) continue;
-            const float ms = time_bucket(P, pos, s, 3);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
+            if (layout(P, s) != NEAT_OK) {
+                cudaGetLastError();
+                continue;
             }
+            const int pos = position_of(hbi);
+            if (pos < 0) continue;
+            timed[hbi].push_back({time_bucket(P, pos, s, 2), c});
         }
         cudaGetLastError();
-        h.shape = best;
-        snprintf(line, sizeof(line), "%s{\"pop\":%d,\"n_class\":%d,\"G\":%d,\"tile\":%d,\"split\":%d,\"ms\":%.5f}",
-                 P->autotune_log.empty() ? "" : ",", h.pop_index, h.n_class, best.G, best.tile, best.split, best_ms);
+        std::sort(timed[hbi].begin(), timed[hbi].end(),
+                  [](const std::pair<float, Shape> &a, const std::pair<float, Shape> &b) { return a.first < b.first; });
+        h.shape = timed[hbi].empty() ? keep : timed[hbi][0].second;
+    }
+    // 2. the whole step: shrink the bucket that sets the block's shared
+    //    memory (it limits every bucket's residency) while that pays
+    int rc = layout(P, s);
+    if (rc) return rc;
+    float best_ms = time_plan(P, s, 2);
+    for (int round = 0; round < 8; ++round) {
+        const int hbi = P->max_footprint_bucket;
+        if (hbi < 0) break;
+        HostBucket &h = P->hb[hbi];
+        const Shape cur = h.shape;
+        const size_t cur_fp = footprint(P, h);
+        bool improved = false;
+        for (const auto &cand : timed[hbi]) {
+            h.shape = cand.second;
+            if (footprint(P, h) >= cur_fp) continue;
+            if (layout(P, s) != NEAT_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            const float ms = time_plan(P, s, 2);
+            if (ms < best_ms) {
+                best_ms = ms;
+                improved = true;
+                break;
+            }
+        }
+        if (!improved) {
+            h.shape = cur;
+            break;
+        }
+    }
+    for (size_t hbi = 0; hbi < P->hb.size(); ++hbi) {
+        const HostBucket &h = P->hb[hbi];
+        snprintf(line, sizeof(line), "%s{\"pop\":%d,\"n_class\":%d,\"G\":%d,\"tile\":%d,\"split\":%d}",
+                 hbi ? "," : "", h.pop_index, h.n_class, h.shape.G, h.shape.tile, h.shape.split);
         P->autotune_log += line;
     }
+    snprintf(line, sizeof(line), ",{\"step_ms\":%.5f}", best_ms);
+    P->autotune_log += line;
     return layout(P, s);
 }
 

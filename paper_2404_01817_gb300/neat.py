@@ -56,6 +56,10 @@ class PopDesc(ctypes.Structure):
                 ("inputs", _P), ("in_step_stride", _i64), ("outputs", _P), ("out_step_stride", _i64)]
 
 
+class Substrate(ctypes.Structure):
+    _fields_ = [("resolution", _i32), ("layers", _i32)]
+
+
 class PlanOptions(ctypes.Structure):
     _fields_ = [("autotune", _i32), ("size_buckets", _i32), ("block_threads", _i32), ("pdl", _i32)]
 
@@ -76,6 +80,7 @@ _sig = {
     "neat_plan_forward_steps": (ctypes.c_int, [_P, _i32, _i32, _P]),
     "neat_plan_describe": (ctypes.c_int, [_P, ctypes.c_char_p, _i32]),
     "neat_plan_destroy": (None, [_P]),
+    "neat_cppn_query": (ctypes.c_int, [_P, _i32, Dims, Substrate, ctypes.c_float, _P, _P]),
     "neat_last_error": (ctypes.c_char_p, []),
     "neat_version": (ctypes.c_char_p, []),
 }
@@ -172,6 +177,18 @@ def neat_forward(transformed, pop: int, d: Dims, inputs, outputs=None, launch: L
                                 ctypes.byref(launch) if launch is not None else None, _stream(stream))
     _check(code, "neat_forward")
     return outputs
+
+
+def neat_cppn_query(transformed, pop: int, d: Dims, resolution: int = 16, layers: int = 3,
+                    threshold: float = 0.2, weights=None, stream=None):
+    """Substrate weights f32 [pop][layers-1][res^2][res^2] of CPPN genomes."""
+    import torch
+    r2 = resolution * resolution
+    if weights is None:
+        weights = torch.empty((pop, layers - 1, r2, r2), dtype=torch.float32, device=transformed.device)
+    _check(_lib.neat_cppn_query(_ptr(transformed), pop, d, Substrate(resolution, layers), threshold,
+                                _ptr(weights), _stream(stream)), "neat_cppn_query")
+    return weights
 
 
 class StepsCache:
