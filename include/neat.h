@@ -328,6 +328,28 @@ NEAT_API int neat_plan_describe(const neat_plan *plan, char *buf_host, int32_t l
 /* Free the plan, its device tables and graphs (after its work completed). */
 NEAT_API void neat_plan_destroy(neat_plan *plan);
 
+/*
+ * Allocation-free batched forward.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a real-time control
+ * loop that must never stall on the device allocator, or a process whose
+ * device memory all belongs to another framework's pool.  It evaluates one
+ * step of up to 64 populations (at most 32768 genomes each) with the same
+ * persistent kernel as neat_plan_forward, one bucket per population and
+ * heuristic launch shapes, and allocates nothing: its scratch (work counter,
+ * bucket table, genome index list; about 136 KB) is a fixed array in device
+ * memory that every GPU loading this library holds until the process exits.
+ * Inputs and outputs are the caller's, as in neat_pop_desc; step s reads
+ * inputs_dev + s * in_step_stride and writes outputs_dev + s * out_step_stride.
+ * The first call on a device, with that device current, looks up the array's
+ * device address and fills its index list (a small kernel on `stream`); make
+ * that first call before any stream capture.  Every call shares the array and
+ * rewrites it: calls that overlap on the GPU (other streams, other threads)
+ * race, so serialise them.  Results equal neat_forward on each population.
+ * Errors: NEAT_EINVAL (more than 64 populations, more than 32768 genomes in
+ * one, a genome too large for one block, bad arguments), NEAT_ECUDA.
+ */
+NEAT_API int neat_forward_multi_noalloc(const neat_pop_desc *pops_host, int32_t npops, int32_t step, void *stream);
+
 /* Description of the last error on this thread ("" if none). */
 NEAT_API const char *neat_last_error(void);
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -693,3 +694,168 @@ int read_plan_error(unsigned int *v, int clear)
     return NEAT_OK;
 }
 }  // namespace neat
+
+// ------------------------------------------------------------------------
+// Allocation-free batched forward: the persistent plan kernel, fed from a
+// fixed scratch array in device memory instead of buffers the plan
+// allocates.  For callers that cannot call cudaMalloc (see neat.h).
+//
+// Scratch layout (file-scope, 256-byte aligned, held by every GPU that loads
+// the library until the process exits):
+//   [0, 256)             the work counter, cleared by every call
+//   [256, idx_off)       the bucket table, written by every call
+//   [idx_off, end)       genome indices 0 .. kNoallocMaxGenomes-1, written once
+// Host code only knows the array through a host-side stand-in, so its device
+// address is fetched with cudaGetSymbolAddress once per device.
+namespace neat {
+namespace {
+
+constexpr int kNoallocMaxPops = 64;
+constexpr int kNoallocMaxGenomes = 32768;
+constexpr size_t kNoallocTableOff = 256;
+constexpr size_t kNoallocIdxOff = kNoallocTableOff + ((sizeof(BucketDev) * kNoallocMaxPops + 255) & ~(size_t)255);
+constexpr size_t kNoallocScratchBytes = kNoallocIdxOff + sizeof(int32_t) * kNoallocMaxGenomes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+__global__ void noalloc_fill_indices(int32_t *idx, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
+}
+
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[256] = {};   // device address of the scratch array, per device id
+
+// Per-device set-up, on the first call made with that device current: the
+// array's device address (cudaGetSymbolAddress) and its index list.
+int noalloc_setup(cudaStream_t s, unsigned char **base)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 256) return invalid("neat_forward_multi_noalloc: device id out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_base[dev]) {
+        *base = g_noalloc_base[dev];
+        return NEAT_OK;
+    }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaGetSymbolAddress");
+    noalloc_fill_indices<<<64, 256, 0, s>>>(reinterpret_cast<int32_t *>(static_cast<unsigned char *>(p) + kNoallocIdxOff),
+                                            kNoallocMaxGenomes);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: index fill");
+    g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+    *base = g_noalloc_base[dev];
+    return NEAT_OK;
+}
+
+}  // namespace
+}  // namespace neat
+
+extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npops, int32_t step, void *stream)
+{
+    clear_error();
+    if (!pops) return invalid("neat_forward_multi_noalloc: null populations");
+    if (npops < 1 || npops > kNoallocMaxPops)
+        return invalid("neat_forward_multi_noalloc: npops must be in 1..64 (the scratch table holds 64 populations)");
+    if (step < 0) return invalid("neat_forward_multi_noalloc: step < 0");
+    for (int p = 0; p < npops; ++p) {
+        const neat_pop_desc &pd = pops[p];
+        if (!dims_ok(pd.dims)) return invalid("neat_forward_multi_noalloc: invalid dims");
+        if (pd.pop < 0 || pd.batch < 0) return invalid("neat_forward_multi_noalloc: pop and batch must be >= 0");
+        if (pd.pop > kNoallocMaxGenomes)
+            return invalid("neat_forward_multi_noalloc: at most 32768 genomes per population (scratch index list)");
+        if (pd.pop > 0 && pd.batch > 0 &&
+            (!pd.transformed_dev || !pd.outputs_dev || (pd.dims.num_inputs > 0 && !pd.inputs_dev)))
+            return invalid("neat_forward_multi_noalloc: null pointer");
+        if (reinterpret_cast<uintptr_t>(pd.transformed_dev) & 15u)
+            return invalid("neat_forward_multi_noalloc: transformed must be 16-byte aligned");
+    }
+    cudaStream_t s = as_stream(stream);
+    unsigned char *base = nullptr;
+    int rc = noalloc_setup(s, &base);
+    if (rc) return rc;
+
+    // one bucket per population, shapes from the heuristic, reserved record size
+    const int NT = 256;
+    BucketDev table[kNoallocMaxPops];
+    int order[kNoallocMaxPops];
+    int nb = 0;
+    for (int p = 0; p < npops; ++p)
+        if (pops[p].pop > 0 && pops[p].batch > 0) order[nb++] = p;
+    for (int i = 1; i < nb; ++i)                    // largest records first
+        for (int j = i; j > 0; --j) {
+            const neat_dims &a = pops[order[j]].dims, &b = pops[order[j - 1]].dims;
+            if (record_max_bytes(a.num_inputs, a.num_outputs, a.max_nodes, a.max_conns) <=
+                record_max_bytes(b.num_inputs, b.num_outputs, b.max_nodes, b.max_conns))
+                break;
+            std::swap(order[j], order[j - 1]);
+        }
+    size_t smem_regions = 0;
+    int cta = 0;
+    for (int i = 0; i < nb; ++i) {
+        const neat_pop_desc &pd = pops[order[i]];
+        const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch);
+        const uint32_t rec = record_max_bytes(pd.dims.num_inputs, pd.dims.num_outputs, pd.dims.max_nodes,
+                                              pd.dims.max_conns);
+        const size_t reg = ((size_t)rec + 4u * (size_t)((pd.dims.max_nodes * sh.tile + 3) & ~3) + 15) & ~(size_t)15;
+        int gpc = NT / sh.G;
+        if (sh.G > 32) gpc = std::min(gpc, 15);
+        while (gpc > 1 && reg * gpc > 200u * 1024u) --gpc;
+        if (reg * gpc + 16u * forward_header_words(NT) > 227u * 1024u)
+            return invalid("neat_forward_multi_noalloc: a population's genome is too large for one block");
+        BucketDev &d = table[i];
+        d.rec = static_cast<const uint8_t *>(pd.transformed_dev);
+        d.gidx = reinterpret_cast<const int32_t *>(base + kNoallocIdxOff);
+        d.x = pd.inputs_dev;
+        d.y = pd.outputs_dev;
+        d.x_step = pd.in_step_stride;
+        d.y_step = pd.out_step_stride;
+        d.stride = record_stride(pd.dims);
+        d.n_genomes = pd.pop;
+        d.I = pd.dims.num_inputs;
+        d.O = pd.dims.num_outputs;
+        d.B = pd.batch;
+        d.tile = sh.tile;
+        d.tiles = (pd.batch + sh.tile - 1) / sh.tile;
+        d.lg_split = lg(sh.split);
+        d.G = sh.G;
+        d.lgG = lg(sh.G);
+        d.gpc = gpc;
+        d.region_words = (int)(reg / 16);
+        d.rec_words = (int)(rec / 16);
+        d.rec_copy_bytes = (int)rec;
+        d.cta_begin = cta;
+        d.cta_items = (int)(((long)d.n_genomes * d.tiles + gpc - 1) / gpc);
+        cta += d.cta_items;
+        smem_regions = std::max(smem_regions, reg * gpc);
+    }
+    if (nb == 0) return NEAT_OK;
+    const size_t smem = smem_regions + 16u * forward_header_words(NT);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, plan_kernel<false>);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaFuncGetAttributes");
+    if (smem + fa.sharedSizeBytes > 227u * 1024u)
+        return invalid("neat_forward_multi_noalloc: shared memory per block exceeds 227 KB");
+    if (smem > 48u * 1024u) {
+        e = cudaFuncSetAttribute(plan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaFuncSetAttribute");
+    }
+    e = cudaMemsetAsync(base, 0, sizeof(unsigned int), s);               // the work counter starts at zero
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: counter reset");
+    e = cudaMemcpyAsync(base + kNoallocTableOff, table, sizeof(BucketDev) * (size_t)nb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: table copy");
+    int dev = 0, sms = 152, smem_sm = 233472;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int per_sm = std::max(1, std::min((int)(smem_sm / (smem + 1024)), 2048 / NT));
+    const int grid = std::max(1, std::min(sms * per_sm, cta));
+    plan_kernel<false><<<grid, NT, smem, s>>>(reinterpret_cast<const BucketDev *>(base + kNoallocTableOff), nb, 0,
+                                              cta, reinterpret_cast<unsigned int *>(base), step);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: launch");
+    return NEAT_OK;
+}

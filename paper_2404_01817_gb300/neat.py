@@ -80,6 +80,7 @@ _sig = {
     "neat_plan_forward_steps": (ctypes.c_int, [_P, _i32, _i32, _P]),
     "neat_plan_describe": (ctypes.c_int, [_P, ctypes.c_char_p, _i32]),
     "neat_plan_destroy": (None, [_P]),
+    "neat_forward_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, _i32, _P]),
     "neat_cppn_query": (ctypes.c_int, [_P, _i32, Dims, Substrate, ctypes.c_float, _P, _P]),
     "neat_last_error": (ctypes.c_char_p, []),
     "neat_version": (ctypes.c_char_p, []),
@@ -273,6 +274,25 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def pop_descs(pops):
+    """neat_pop_desc array for dicts as taken by Plan (kept alive by the caller)."""
+    descs = (PopDesc * len(pops))()
+    for i, p in enumerate(pops):
+        x, y = p["inputs"], p["outputs"]
+        batch = x.shape[-2]
+        d = p["dims"]
+        in_step = x.shape[-3] * batch * d.num_inputs if x.dim() == 4 else 0
+        out_step = y.shape[-3] * batch * d.num_outputs if y.dim() == 4 else 0
+        descs[i] = PopDesc(_ptr(p["transformed"]), p["pop"], d, batch, _ptr(x), in_step, _ptr(y), out_step)
+    return descs
+
+
+def neat_forward_multi_noalloc(pops, step: int = 0, stream=None):
+    """One step of several populations through the allocation-free entry point."""
+    descs = pop_descs(pops)
+    _check(_lib.neat_forward_multi_noalloc(descs, len(pops), step, _stream(stream)), "neat_forward_multi_noalloc")
 
 
 # ----------------------------------------------------------- record decoding
