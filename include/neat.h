@@ -350,6 +350,75 @@ NEAT_API void neat_plan_destroy(neat_plan *plan);
  */
 NEAT_API int neat_forward_multi_noalloc(const neat_pop_desc *pops_host, int32_t npops, int32_t step, void *stream);
 
+/* ------------------------------------------------------------- serving
+ *
+ * Continuous batching of evaluation requests.  The server owns one device
+ * pool of hbm_budget_bytes (allocated at create) and a scheduler thread.
+ * Queued requests are admitted, in arrival order (a later one that fits may
+ * pass one that does not), as pool memory frees up; their genome tensors are
+ * copied in and transformed once.  Every scheduler tick advances each active
+ * request by one step -- one kernel generating the step's observations, one
+ * persistent-kernel launch evaluating all active requests together -- so
+ * requests that arrive while others run share the device with them.  A
+ * request's outputs are identical alone and in any mix.  Observations of step
+ * s are N(0,1) values from a counter-based generator (Philox-4x32-10 with a
+ * Box-Muller transform) keyed by the request's seed: neat_fill_normal
+ * reproduces them.  Times are host steady-clock milliseconds.
+ */
+typedef struct neat_serve_cfg {
+    uint64_t hbm_budget_bytes;  /* device pool for admitted requests */
+    int32_t max_active;         /* requests evaluated together per tick, 1..4096 */
+    int32_t reserved;
+} neat_serve_cfg;
+
+typedef struct neat_request {
+    const float *nodes_host;    /* [pop][max_nodes][5], copied by submit */
+    const float *conns_host;    /* [pop][max_conns][4], copied by submit */
+    int32_t pop;                /* 1..65536 */
+    neat_dims dims;
+    int32_t batch;              /* input vectors per genome per step, >= 1 */
+    int32_t steps;              /* >= 1 */
+    uint64_t obs_seed;          /* observations of step s: neat_fill_normal(obs_seed, s, pop*batch*I) */
+    float *outputs_dev;         /* caller-owned until done; step s writes outputs_dev + s * out_step_stride */
+    int64_t out_step_stride;    /* floats; 0: every step overwrites [pop][batch][O] */
+} neat_request;
+
+typedef struct neat_result {
+    int32_t status;             /* NEAT_OK or NEAT_ECANCELLED */
+    int32_t reserved;
+    double submit_ms, admit_ms, done_ms;
+    uint64_t genome_forwards;   /* pop * batch * steps evaluated */
+} neat_result;
+
+typedef struct neat_serve_report {
+    int32_t completed, cancelled, queued, active;
+    double latency_p50_ms, latency_p99_ms;        /* submit -> last step done */
+    double queue_wait_p50_ms, queue_wait_p99_ms;  /* submit -> admitted */
+    uint64_t genome_forwards;
+    double genome_forwards_per_s;                 /* over first submit .. last completion */
+    int64_t ticks;
+    uint64_t pool_used_bytes;
+} neat_serve_report;
+
+typedef struct neat_server neat_server;
+
+/* Create a server on the current device.  Errors: NEAT_EINVAL, NEAT_ENOMEM, NEAT_ECUDA. */
+NEAT_API int neat_serve_create(const neat_serve_cfg *cfg_host, neat_server **out_host);
+/* Queue a request (the genome tensors are copied; caller buffers may be
+ * reused on return).  NEAT_EBUDGET if it can never fit the pool. */
+NEAT_API int neat_serve_submit(neat_server *srv, const neat_request *req_host, uint64_t *ticket_host);
+/* NEAT_EAGAIN until the request is done; then its status and *res. */
+NEAT_API int neat_serve_poll(neat_server *srv, uint64_t ticket, neat_result *res_host);
+/* Block up to timeout_ms; NEAT_ETIMEOUT if still not done. */
+NEAT_API int neat_serve_wait(neat_server *srv, uint64_t ticket, int32_t timeout_ms, neat_result *res_host);
+/* Cancel: a queued request is dropped, an active one stops after its steps in flight. */
+NEAT_API int neat_serve_cancel(neat_server *srv, uint64_t ticket);
+NEAT_API int neat_serve_stats(neat_server *srv, neat_serve_report *st_host);
+/* Cancel what is left, drain the device, free everything. */
+NEAT_API void neat_serve_destroy(neat_server *srv);
+/* The serving observations: count N(0,1) floats of (seed, step) into out_dev. */
+NEAT_API int neat_fill_normal(uint64_t seed, int32_t step, int64_t count, float *out_dev, void *stream);
+
 /* Description of the last error on this thread ("" if none). */
 NEAT_API const char *neat_last_error(void);
 

@@ -71,6 +71,34 @@ int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d,
                       const float *inputs, int32_t batch, float *outputs,
                       const neat_launch &L, ForwardArgs *out);
 int check_launch(const neat_launch &L);
+
+// One bucket of the persistent multi-population kernel (neat_plan.cu): a
+// set of genomes of one population evaluated with one launch shape.
+struct BucketDev {
+    const uint8_t *rec;
+    const int32_t *gidx;     // genome indices (within the population) of this bucket
+    const float *x;
+    float *y;
+    int64_t x_step, y_step;  // floats between steps
+    uint64_t stride;
+    int n_genomes;
+    int I, O, B;
+    int tile, tiles, lg_split;
+    int G, lgG, gpc;
+    int region_words;        // 16-byte words of one group's region (record + values)
+    int rec_words;           // 16-byte words reserved for the record
+    int rec_copy_bytes;
+    int cta_begin, cta_items;
+};
+
+// A whole population as one bucket with the heuristic launch shape; gidx_dev
+// must list genomes 0..pop-1.  *footprint: shared memory of its groups.
+int fill_population_bucket(const neat_pop_desc &pd, const int32_t *gidx_dev, int block_threads, int cta_begin,
+                           BucketDev *out, size_t *footprint);
+// Launch the persistent kernel over a bucket table already in device memory
+// (counter_dev must be zero).
+int launch_plan_table(const BucketDev *table_dev, int nb, int total_items, unsigned int *counter_dev, int step,
+                      size_t smem_regions, int block_threads, cudaStream_t s);
 int read_plan_error(unsigned int *v, int clear);   // neat_plan.cu
 int read_cppn_error(unsigned int *v, int clear);   // neat_cppn.cu
 

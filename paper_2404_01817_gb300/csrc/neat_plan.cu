@@ -28,23 +28,6 @@
 namespace neat {
 namespace {
 
-struct BucketDev {
-    const uint8_t *rec;
-    const int32_t *gidx;     // genome indices (within the population) of this bucket
-    const float *x;
-    float *y;
-    int64_t x_step, y_step;  // floats between steps
-    uint64_t stride;
-    int n_genomes;
-    int I, O, B;
-    int tile, tiles, lg_split;
-    int G, lgG, gpc;
-    int region_words;        // 16-byte words of one group's region (record + values)
-    int rec_words;           // 16-byte words reserved for the record
-    int rec_copy_bytes;
-    int cta_begin, cta_items;
-};
-
 __device__ unsigned int g_plan_error;
 
 template <bool PDL>
@@ -859,3 +842,73 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
     if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: launch");
     return NEAT_OK;
 }
+
+// ------------------------------------------------------------------------
+// Internal helpers for other translation units (the serving runtime).
+namespace neat {
+
+int fill_population_bucket(const neat_pop_desc &pd, const int32_t *gidx_dev, int block_threads, int cta_begin,
+                           BucketDev *out, size_t *footprint)
+{
+    const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch);
+    const uint32_t rec = record_max_bytes(pd.dims.num_inputs, pd.dims.num_outputs, pd.dims.max_nodes,
+                                          pd.dims.max_conns);
+    const size_t reg = ((size_t)rec + 4u * (size_t)((pd.dims.max_nodes * sh.tile + 3) & ~3) + 15) & ~(size_t)15;
+    int gpc = block_threads / sh.G;
+    if (sh.G > 32) gpc = std::min(gpc, 15);
+    while (gpc > 1 && reg * gpc > 200u * 1024u) --gpc;
+    if (gpc < 1 || reg * gpc + 16u * forward_header_words(block_threads) > 227u * 1024u)
+        return invalid("a genome of this size does not fit one block");
+    BucketDev &d = *out;
+    d.rec = static_cast<const uint8_t *>(pd.transformed_dev);
+    d.gidx = gidx_dev;
+    d.x = pd.inputs_dev;
+    d.y = pd.outputs_dev;
+    d.x_step = pd.in_step_stride;
+    d.y_step = pd.out_step_stride;
+    d.stride = record_stride(pd.dims);
+    d.n_genomes = pd.pop;
+    d.I = pd.dims.num_inputs;
+    d.O = pd.dims.num_outputs;
+    d.B = pd.batch;
+    d.tile = sh.tile;
+    d.tiles = (pd.batch + sh.tile - 1) / sh.tile;
+    d.lg_split = lg(sh.split);
+    d.G = sh.G;
+    d.lgG = lg(sh.G);
+    d.gpc = gpc;
+    d.region_words = (int)(reg / 16);
+    d.rec_words = (int)(rec / 16);
+    d.rec_copy_bytes = (int)rec;
+    d.cta_begin = cta_begin;
+    d.cta_items = (int)(((long)d.n_genomes * d.tiles + gpc - 1) / gpc);
+    *footprint = reg * gpc;
+    return NEAT_OK;
+}
+
+int launch_plan_table(const BucketDev *table_dev, int nb, int total_items, unsigned int *counter_dev, int step,
+                      size_t smem_regions, int block_threads, cudaStream_t s)
+{
+    if (nb == 0 || total_items == 0) return NEAT_OK;
+    const size_t smem = smem_regions + 16u * forward_header_words(block_threads);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, plan_kernel<false>);
+    if (e != cudaSuccess) return cuda_fail(e, "plan table: cudaFuncGetAttributes");
+    if (smem + fa.sharedSizeBytes > 227u * 1024u) return invalid("plan table: shared memory exceeds 227 KB");
+    if (smem > 48u * 1024u) {
+        e = cudaFuncSetAttribute(plan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "plan table: cudaFuncSetAttribute");
+    }
+    int dev = 0, sms = 152, smem_sm = 233472;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int per_sm = std::max(1, std::min((int)(smem_sm / (smem + 1024)), 2048 / block_threads));
+    const int grid = std::max(1, std::min(sms * per_sm, total_items));
+    plan_kernel<false><<<grid, block_threads, smem, s>>>(table_dev, nb, 0, total_items, counter_dev, step);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "plan table: launch");
+    return NEAT_OK;
+}
+
+}  // namespace neat

@@ -60,6 +60,28 @@ class Substrate(ctypes.Structure):
     _fields_ = [("resolution", _i32), ("layers", _i32)]
 
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active", _i32), ("reserved", _i32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("nodes_host", _P), ("conns_host", _P), ("pop", _i32), ("dims", Dims), ("batch", _i32),
+                ("steps", _i32), ("obs_seed", ctypes.c_uint64), ("outputs_dev", _P), ("out_step_stride", _i64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", _i32), ("reserved", _i32), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("genome_forwards", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", _i32), ("cancelled", _i32), ("queued", _i32), ("active", _i32),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("queue_wait_p50_ms", ctypes.c_double), ("queue_wait_p99_ms", ctypes.c_double),
+                ("genome_forwards", ctypes.c_uint64), ("genome_forwards_per_s", ctypes.c_double),
+                ("ticks", _i64), ("pool_used_bytes", ctypes.c_uint64)]
+
+
 class PlanOptions(ctypes.Structure):
     _fields_ = [("autotune", _i32), ("size_buckets", _i32), ("block_threads", _i32), ("pdl", _i32)]
 
@@ -82,6 +104,14 @@ _sig = {
     "neat_plan_destroy": (None, [_P]),
     "neat_forward_multi_noalloc": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, _i32, _P]),
     "neat_cppn_query": (ctypes.c_int, [_P, _i32, Dims, Substrate, ctypes.c_float, _P, _P]),
+    "neat_serve_create": (ctypes.c_int, [ctypes.POINTER(ServeCfg), ctypes.POINTER(_P)]),
+    "neat_serve_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "neat_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "neat_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _i32, ctypes.POINTER(Result)]),
+    "neat_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "neat_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServeStats)]),
+    "neat_serve_destroy": (None, [_P]),
+    "neat_fill_normal": (ctypes.c_int, [ctypes.c_uint64, _i32, _i64, _P, _P]),
     "neat_last_error": (ctypes.c_char_p, []),
     "neat_version": (ctypes.c_char_p, []),
 }
@@ -274,6 +304,59 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """neat_serve_*: continuous batching of evaluation requests under an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 256):
+        self.handle = _P(None)
+        cfg = ServeCfg(hbm_budget_bytes, max_active, 0)
+        _check(_lib.neat_serve_create(ctypes.byref(cfg), ctypes.byref(self.handle)), "neat_serve_create")
+
+    def submit(self, nodes: np.ndarray, conns: np.ndarray, d: Dims, batch: int, steps: int, obs_seed: int,
+               outputs, out_step_stride: int = 0) -> int:
+        nodes = np.ascontiguousarray(nodes, dtype=np.float32)
+        conns = np.ascontiguousarray(conns, dtype=np.float32)
+        req = Request(nodes.ctypes.data, conns.ctypes.data, nodes.shape[0], d, batch, steps, obs_seed,
+                      _ptr(outputs), out_step_stride)
+        t = ctypes.c_uint64(0)
+        _check(_lib.neat_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "neat_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        r = Result()
+        code = _lib.neat_serve_poll(self.handle, ticket, ctypes.byref(r))
+        return code, r
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        r = Result()
+        code = _lib.neat_serve_wait(self.handle, ticket, timeout_ms, ctypes.byref(r))
+        return code, r
+
+    def cancel(self, ticket: int):
+        _check(_lib.neat_serve_cancel(self.handle, ticket), "neat_serve_cancel")
+
+    def stats(self) -> ServeStats:
+        st = ServeStats()
+        _check(_lib.neat_serve_stats(self.handle, ctypes.byref(st)), "neat_serve_stats")
+        return st
+
+    def close(self):
+        if self.handle.value:
+            _lib.neat_serve_destroy(self.handle)
+            self.handle = _P(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def neat_fill_normal(seed: int, step: int, out, stream=None):
+    _check(_lib.neat_fill_normal(seed, step, out.numel(), _ptr(out), _stream(stream)), "neat_fill_normal")
+    return out
 
 
 def pop_descs(pops):
