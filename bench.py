@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
-    ap.add_argument("--workload", choices=["ant", "batched", "cppn"], default="ant",
+    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving"], default="ant",
                     help="ant: the headline line; batched / cppn: the uneven-batch and CPPN shapes")
     return ap.parse_args()
 
@@ -288,6 +288,71 @@ def run_cppn(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, n_requests=400, n_templates=16):
+    """Serving: a Poisson stream (200 requests/s) of requests with log-uniform
+    population (64-4096), max nodes (8-512) and batch (1-256), 100 steps each,
+    through neat_serve_* at HBM budgets of 1, 4 and 16 GB.  Genomes come from
+    16 request templates drawn from that distribution (request i uses
+    template i mod 16 with its own observation seed), held in pinned memory and
+    lent to the server."""
+    import threading
+
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    reqs = W.serving_requests(0, n_requests)
+    tmpl = []
+    for k in range(n_templates):
+        r = reqs[k]
+        p = W.request_population(r)
+        nodes = torch.from_numpy(p.nodes).pin_memory()
+        conns = torch.from_numpy(p.conns).pin_memory()
+        d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
+        y = torch.empty((p.pop, r["batch"], p.num_outputs), device=dev)
+        tmpl.append(dict(r=r, nodes=nodes.numpy(), conns=conns.numpy(), keep=(nodes, conns), dims=d, y=y))
+    results = {}
+    for budget_gb in (1, 4, 16):
+        srv = neat.Server(budget_gb << 30, max_active=256)
+        t = tmpl[0]
+        srv.wait(srv.submit(t["nodes"], t["conns"], t["dims"], t["r"]["batch"], 2, 1, t["y"], borrow=True))
+        srv.close()
+        srv = neat.Server(budget_gb << 30, max_active=256)
+        tickets = []
+
+        def client():
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                dt = r["arrival_s"] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                t = tmpl[i % n_templates]
+                tickets.append(srv.submit(t["nodes"], t["conns"], t["dims"], t["r"]["batch"], 100, 7919 * i + 1,
+                                          t["y"], borrow=True))
+        with ClockSampler(0) as clocks:
+            th = threading.Thread(target=client)
+            th.start()
+            th.join()
+            for tk in tickets:
+                srv.wait(tk, 600000)
+        st = srv.stats()
+        results[f"{budget_gb}GB"] = {"latency_p50_ms": st.latency_p50_ms, "latency_p99_ms": st.latency_p99_ms,
+                                     "queue_wait_p50_ms": st.queue_wait_p50_ms,
+                                     "queue_wait_p99_ms": st.queue_wait_p99_ms, "completed": st.completed,
+                                     "genome_forwards_per_s": st.genome_forwards_per_s, "ticks": st.ticks,
+                                     "clocks": clocks.summary()}
+        srv.close()
+    best = results["16GB"]
+    line = {"metric": "serving: genome-forwards/s and request latency p50/p99 ms (Poisson 200 req/s)",
+            "value": best["genome_forwards_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving", "requests": n_requests, "rate_hz": 200, "steps_per_request": 100,
+                       "templates": n_templates},
+            "latency_ms": {"p50": best["latency_p50_ms"], "p99": best["latency_p99_ms"]},
+            "budgets": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -298,6 +363,9 @@ def main():
         return
     if args.workload == "cppn":
         run_cppn(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     import torch
     rank, local_rank, world = dist_env()

@@ -378,10 +378,16 @@ typedef struct neat_request {
     neat_dims dims;
     int32_t batch;              /* input vectors per genome per step, >= 1 */
     int32_t steps;              /* >= 1 */
+    int32_t flags;              /* NEAT_REQ_* */
     uint64_t obs_seed;          /* observations of step s: neat_fill_normal(obs_seed, s, pop*batch*I) */
     float *outputs_dev;         /* caller-owned until done; step s writes outputs_dev + s * out_step_stride */
     int64_t out_step_stride;    /* floats; 0: every step overwrites [pop][batch][O] */
 } neat_request;
+
+/* neat_request.flags: the server reads nodes_host/conns_host in place (no
+ * copy at submit); they must stay valid until the request is done.  With
+ * pinned host memory the copy at admission is asynchronous. */
+#define NEAT_REQ_BORROW_HOST 1
 
 typedef struct neat_result {
     int32_t status;             /* NEAT_OK or NEAT_ECANCELLED */
@@ -404,8 +410,9 @@ typedef struct neat_server neat_server;
 
 /* Create a server on the current device.  Errors: NEAT_EINVAL, NEAT_ENOMEM, NEAT_ECUDA. */
 NEAT_API int neat_serve_create(const neat_serve_cfg *cfg_host, neat_server **out_host);
-/* Queue a request (the genome tensors are copied; caller buffers may be
- * reused on return).  NEAT_EBUDGET if it can never fit the pool. */
+/* Queue a request (the genome tensors are copied, unless NEAT_REQ_BORROW_HOST;
+ * caller buffers may then be reused on return).  NEAT_EBUDGET if it can
+ * never fit the pool. */
 NEAT_API int neat_serve_submit(neat_server *srv, const neat_request *req_host, uint64_t *ticket_host);
 /* NEAT_EAGAIN until the request is done; then its status and *res. */
 NEAT_API int neat_serve_poll(neat_server *srv, uint64_t ticket, neat_result *res_host);

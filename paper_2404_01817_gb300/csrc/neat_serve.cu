@@ -335,11 +335,13 @@ void worker_main(neat_server *S)
         for (Request *R : admitted) {
             unsigned char *base = S->pool + R->off;
             const neat_request &r = R->r;
-            e = cudaMemcpyAsync(base + R->o_nodes, R->nodes.data(), R->nodes.size() * 4, cudaMemcpyHostToDevice,
-                                S->stream);
-            if (e == cudaSuccess && !R->conns.empty())
-                e = cudaMemcpyAsync(base + R->o_conns, R->conns.data(), R->conns.size() * 4, cudaMemcpyHostToDevice,
-                                    S->stream);
+            const bool borrow = (r.flags & NEAT_REQ_BORROW_HOST) != 0;
+            const float *hn = borrow ? r.nodes_host : R->nodes.data();
+            const float *hc = borrow ? r.conns_host : R->conns.data();
+            const size_t nn = (size_t)r.pop * r.dims.max_nodes * 5, nc = (size_t)r.pop * r.dims.max_conns * 4;
+            e = cudaMemcpyAsync(base + R->o_nodes, hn, nn * 4, cudaMemcpyHostToDevice, S->stream);
+            if (e == cudaSuccess && nc)
+                e = cudaMemcpyAsync(base + R->o_conns, hc, nc * 4, cudaMemcpyHostToDevice, S->stream);
             int rc = neat_transform(reinterpret_cast<float *>(base + R->o_nodes),
                                     reinterpret_cast<float *>(base + R->o_conns), r.pop, r.dims, base + R->o_rec,
                                     record_stride(r.dims) * (size_t)r.pop,
@@ -464,9 +466,11 @@ extern "C" int neat_serve_submit(neat_server *S, const neat_request *r, uint64_t
         size_t fp;
         if (fill_population_bucket(pd, nullptr, S->block_threads, 0, &tmp, &fp) != NEAT_OK) return NEAT_EINVAL;
     }
-    R->nodes.assign(r->nodes_host, r->nodes_host + (size_t)r->pop * r->dims.max_nodes * 5);
-    R->conns.assign(r->conns_host ? r->conns_host : r->nodes_host,
-                    (r->conns_host ? r->conns_host : r->nodes_host) + (size_t)r->pop * r->dims.max_conns * 4);
+    if (!(r->flags & NEAT_REQ_BORROW_HOST)) {
+        R->nodes.assign(r->nodes_host, r->nodes_host + (size_t)r->pop * r->dims.max_nodes * 5);
+        R->conns.assign(r->conns_host ? r->conns_host : r->nodes_host,
+                        (r->conns_host ? r->conns_host : r->nodes_host) + (size_t)r->pop * r->dims.max_conns * 4);
+    }
     R->t_submit = now_ms();
     std::lock_guard<std::mutex> lk(S->mu);
     R->ticket = S->next_ticket++;

@@ -66,7 +66,11 @@ class ServeCfg(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("nodes_host", _P), ("conns_host", _P), ("pop", _i32), ("dims", Dims), ("batch", _i32),
-                ("steps", _i32), ("obs_seed", ctypes.c_uint64), ("outputs_dev", _P), ("out_step_stride", _i64)]
+                ("steps", _i32), ("flags", _i32), ("obs_seed", ctypes.c_uint64), ("outputs_dev", _P),
+                ("out_step_stride", _i64)]
+
+
+REQ_BORROW_HOST = 1
 
 
 class Result(ctypes.Structure):
@@ -315,11 +319,13 @@ class Server:
         _check(_lib.neat_serve_create(ctypes.byref(cfg), ctypes.byref(self.handle)), "neat_serve_create")
 
     def submit(self, nodes: np.ndarray, conns: np.ndarray, d: Dims, batch: int, steps: int, obs_seed: int,
-               outputs, out_step_stride: int = 0) -> int:
+               outputs, out_step_stride: int = 0, borrow: bool = False) -> int:
+        """Queue a request; with borrow=True the host arrays must stay alive
+        (and unchanged) until the request is done."""
         nodes = np.ascontiguousarray(nodes, dtype=np.float32)
         conns = np.ascontiguousarray(conns, dtype=np.float32)
-        req = Request(nodes.ctypes.data, conns.ctypes.data, nodes.shape[0], d, batch, steps, obs_seed,
-                      _ptr(outputs), out_step_stride)
+        req = Request(nodes.ctypes.data, conns.ctypes.data, nodes.shape[0], d, batch, steps,
+                      REQ_BORROW_HOST if borrow else 0, obs_seed, _ptr(outputs), out_step_stride)
         t = ctypes.c_uint64(0)
         _check(_lib.neat_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "neat_serve_submit")
         return t.value
