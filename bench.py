@@ -394,9 +394,12 @@ def main():
     L_plain = neat.neat_default_launch(POP, d, 1)
     L_batched = neat.neat_default_launch(POP, d, 1)
     L_batched.pdl = 1
+    order = torch.empty(POP, dtype=torch.int32, device=dev)
+    L_batched.order_dev = order.data_ptr()
 
     def episode_batched():
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        neat.neat_schedule(rec, POP, d, order, stream=stream)
         neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
 
     def episode_plain(step_events=None):
@@ -422,6 +425,7 @@ def main():
 
     if args.profile:
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        neat.neat_schedule(rec, POP, d, order, stream=stream)
         for s in range(3):
             neat.neat_forward(rec, POP, d, obs[s], act[s], launch=L_plain, stream=stream)
         neat.neat_forward_steps(rec, POP, d, obs[:8], act[:8], cache, launch=L_batched, stream=stream)
@@ -449,6 +453,7 @@ def main():
         for k in range(args.steps):
             ep_events[k][0].record(stream)
             neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+            neat.neat_schedule(rec, POP, d, order, stream=stream)
             fw_events[k][0].record(stream)
             neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
             fw_events[k][1].record(stream)
@@ -523,7 +528,8 @@ def main():
                                "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + "
                                f"{S} sequential forwards (1 obs/genome/step)",
                    "l2": "inputs larger than L2 (1.08 GB of observations per bench step)",
-                   "form": "batched: CUDA graph of the steps with programmatic dependent launch",
+                   "form": "batched: CUDA graph of the steps with programmatic dependent launch, genomes in "
+                           "depth order (neat_schedule)",
                    "launch": {"group": L_batched.group, "tile": L_batched.tile,
                               "groups_per_block": L_batched.groups_per_block}},
         "plain": {"value": value_plain, "unit": UNIT, "episodes": n_plain,
@@ -532,7 +538,7 @@ def main():
                        "step_mean_batched": statistics.mean(fw_ms) / S},
         "e2e": {"value": world * POP * S * n_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": n_e2e},
-        "gpu_launches": args.steps * (1 + S),
+        "gpu_launches": args.steps * (2 + S),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
                      "kernel": "forward_kernel (batched form, per launch, graph-amortised)",

@@ -217,7 +217,19 @@ typedef struct neat_launch {
     int32_t pdl;
     int32_t split;   /* tile == 1: at most this many threads (1, 2 or 4) share one node's edges,
                         chosen per level from its width; else ignored (1) */
+    int32_t reserved;
+    const int32_t *order_dev;   /* optional genome order (device, a permutation of 0..pop-1, e.g.
+                                   from neat_schedule): work item k evaluates genome order_dev[k];
+                                   outputs stay in genome order.  NULL: identity */
 } neat_launch;
+
+/*
+ * Genome order for the forward: genomes sorted by level count, deepest
+ * first, into order_dev (int32 [pop], device).  Groups that share a warp then
+ * walk similar numbers of levels.  Reads the record headers only; runs on
+ * `stream` (one block).  The order changes speed, never results.
+ */
+NEAT_API int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims d, int32_t *order_dev, void *stream);
 
 /* The launch shape neat_forward uses for (pop, d, batch): the smallest
  * number of waves on the current device, genomes spread evenly over its SMs. */

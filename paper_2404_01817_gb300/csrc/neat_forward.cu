@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
 
     const long item = (long)blockIdx.x * gpb + gi;
     if (item >= (long)a.pop * a.tiles) return;
-    const int g = (int)(item / a.tiles);
-    const int b0 = (int)(item - (long)g * a.tiles) * a.tile;
+    const int k = (int)(item / a.tiles);
+    const int g = a.order ? __ldg(a.order + k) : k;
+    const int b0 = (int)(item - (long)k * a.tiles) * a.tile;
     const int bt = T1 ? 1 : min(a.tile, a.B - b0);
 
     // one bulk copy of the genome's record into shared memory; records do
@@ -69,6 +70,108 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
     }
     run_item<T1>(srec, v, bar, flags + gi, G, gi, lane, a.x + ((size_t)g * a.B + b0) * a.I,
                  a.y + ((size_t)g * a.B + b0) * a.O, a.I, a.O, bt, a.tile, a.lg_split, &g_forward_error);
+}
+
+// One thread per genome (group 1, tile 1): each thread walks the positions
+// of its own genome in order, so no barrier is needed between levels; the
+// loops run warp-uniform trip counts (the warp's largest position count and,
+// per position, its largest in-degree) with predicated edge loads, which
+// keeps the warp converged while 32 genomes advance together.  Same
+// aggregation order as every other shape (four partials, fixed tree).
+constexpr int kSerialInputs = 32;
+
+template <bool FAST>
+__device__ __forceinline__ void walk_serial(const uint4 *srec, float *v, int npos, int first, unsigned mask)
+{
+    const uint4 h1 = srec[1];
+    const uint4 *nodes = srec + 2;
+    const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
+    const int maxpos = (int)__reduce_max_sync(mask, (unsigned)max(npos, 0));
+    for (int it = 0; it < maxpos; ++it) {
+        const int p = first + it;
+        uint4 ne = make_uint4(0u, 0u, 0u, (uint32_t)kInputAct);
+        if (it < npos) ne = nodes[p];
+        const uint32_t act = ne.w & 0xffu;
+        const bool live = act != kInputAct;
+        const uint32_t ec = live ? (ne.z >> 16) : 0u;
+        const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
+        const uint2 *e = edges + (ne.z & 0xffffu);
+        const uint32_t ecmax = __reduce_max_sync(mask, ec);
+        const float id = FAST ? 0.0f : agg_identity(agg);
+        float q0 = id, q1 = id, q2 = id, q3 = id;
+        for (uint32_t i = 0; i < ecmax; i += 4) {
+            if (i < ec) { const uint2 t = e[i]; q0 = agg_step(agg, q0, __uint_as_float(t.x), v[t.y]); }
+            if (i + 1 < ec) { const uint2 t = e[i + 1]; q1 = agg_step(agg, q1, __uint_as_float(t.x), v[t.y]); }
+            if (i + 2 < ec) { const uint2 t = e[i + 2]; q2 = agg_step(agg, q2, __uint_as_float(t.x), v[t.y]); }
+            if (i + 3 < ec) { const uint2 t = e[i + 3]; q3 = agg_step(agg, q3, __uint_as_float(t.x), v[t.y]); }
+        }
+        const float a = agg_combine(agg, agg_combine(agg, q0, q1), agg_combine(agg, q2, q3));
+        if (live)
+            v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                        : node_output(ne, agg, act, ec, a);
+    }
+}
+
+template <bool PDL>
+__global__ void __launch_bounds__(1024, 1) forward_serial_kernel(const ForwardArgs a)
+{
+    extern __shared__ __align__(16) uint4 smem[];
+    const int gpb = blockDim.x;
+    const int gi = threadIdx.x;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    uint4 *srec = smem + forward_header_words(gpb) + (size_t)gi * (a.rec_words + a.val_floats / 4);
+    float *v = reinterpret_cast<float *>(srec + a.rec_words);
+    // lanes of this warp that exist in the block (the last warp may be partial)
+    const int wbase = threadIdx.x & ~31;
+    const int wn = min(32, gpb - wbase);
+    const unsigned mask = wn == 32 ? 0xffffffffu : ((1u << wn) - 1u);
+
+    const long k = (long)blockIdx.x * gpb + gi;
+    const bool valid = k < a.pop;
+    const long g = valid && a.order ? (long)__ldg(a.order + k) : k;
+    const uint8_t *grec = a.rec + (size_t)(valid ? g : 0) * a.stride;
+    const uint32_t bar = smem_addr(bars + gi);
+    if (valid) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, (uint32_t)a.rec_copy_bytes);
+        bulk_g2s(smem_addr(srec), grec, (uint32_t)a.rec_copy_bytes, bar);
+    }
+    if constexpr (PDL) {
+        pdl_wait();
+        pdl_trigger();
+    }
+    const float *xb = a.x + (size_t)(valid ? g : 0) * a.B * a.I;
+    float xr[kSerialInputs];
+#pragma unroll
+    for (int k = 0; k < kSerialInputs; ++k) xr[k] = (valid && k < a.I) ? __ldg(xb + k) : 0.0f;
+    bool ok = valid && mbar_wait(bar, 0);
+    if (valid && !ok) {
+        atomicOr(&g_forward_error, kErrWaitExpired);
+        mbar_wait(bar, 0);
+    }
+    int npos = 0, first = 0;
+    uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
+    if (ok) {
+        h0 = srec[0];
+        h1 = srec[1];
+        ok = (h0.z & NEAT_G_ERROR_MASK) == 0;
+    }
+    const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
+    if (ok) {
+        first = (int)(h0.w >> 16);
+        npos = (int)(h0.x & 0xffffu) - first;
+#pragma unroll
+        for (int k = 0; k < kSerialInputs; ++k)
+            if (k < a.I) v[io[k]] = xr[k];
+        for (int k = kSerialInputs; k < a.I; ++k) v[io[k]] = __ldg(xb + k);
+    }
+    // every lane of the warp takes part in the walk's warp-uniform loop counts
+    if ((h0.w & 0xffffu) == kTraitsSumTanh) walk_serial<true>(srec, v, npos, first, mask);
+    else walk_serial<false>(srec, v, npos, first, mask);
+    if (valid) {
+        float *yb = a.y + (size_t)g * a.B * a.O;
+        for (int j = 0; j < a.O; ++j) yb[j] = ok ? v[io[a.I + j]] : __int_as_float(0x7fc00000);
+    }
 }
 
 using KernelFn = void (*)(ForwardArgs);
@@ -141,6 +244,7 @@ int make_forward_args(const void *transformed, int32_t pop, const neat_dims &d, 
     a.rec_words = (int)(record_max_bytes(a.I, a.O, a.N, d.max_conns) / 16);
     a.val_floats = (a.N * L.tile + 3) & ~3;
     a.rec_copy_bytes = (a.rec_words * 16 <= kOnePieceRecordBytes) ? a.rec_words * 16 : 0;
+    a.order = L.order_dev;
     *out = a;
     return NEAT_OK;
 }
@@ -153,6 +257,11 @@ int launch_forward(const ForwardArgs &a, const neat_launch &L, cudaStream_t s)
     const size_t smem = per_group * L.groups_per_block + 16u * (size_t)forward_header_words(L.groups_per_block);
     if (smem > 227 * 1024) return invalid("forward: shared memory per block exceeds 227 KB; lower tile or groups_per_block");
     KernelFn f = pick(L.pdl != 0, a.tile == 1);
+    if (L.group == 1 && a.tile == 1) {
+        // one thread per genome; the whole record is copied in one piece
+        if (a.rec_copy_bytes == 0) return invalid("forward: group 1 needs records of at most 8 KB");
+        f = L.pdl ? forward_serial_kernel<true> : forward_serial_kernel<false>;
+    }
     int rc = ensure_smem(f, smem);
     if (rc) return rc;
     const long grid = (items + L.groups_per_block - 1) / L.groups_per_block;
@@ -254,6 +363,8 @@ extern "C" int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat
     neat_launch L;
     const int N = d.max_nodes;
     L.split = 1;
+    L.reserved = 0;
+    L.order_dev = nullptr;
     if (batch <= 1) {
         L.tile = 1;
         L.group = N <= 64 ? 8 : (N <= 256 ? 16 : 32);
@@ -319,7 +430,7 @@ static bool same_key(const neat_steps_cache &c, const void *rec, int32_t pop, co
            c.d.num_outputs == d.num_outputs && c.d.max_nodes == d.max_nodes && c.d.max_conns == d.max_conns &&
            c.x == x && c.xs == xs && c.batch == batch && c.y == y && c.ys == ys && c.steps == steps &&
            c.L.group == L.group && c.L.tile == L.tile && c.L.groups_per_block == L.groups_per_block &&
-           c.L.pdl == L.pdl && c.L.split == L.split;
+           c.L.pdl == L.pdl && c.L.split == L.split && c.L.order_dev == L.order_dev;
 }
 
 extern "C" int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_dims d, const float *inputs_dev,
@@ -418,5 +529,55 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
     if (rc == NEAT_OK) rc = read_cppn_error(&vc, clear);
     if (rc) return rc;
     *out_host = v | vp | vc;
+    return NEAT_OK;
+}
+
+// ------------------------------------------------------------ genome order
+
+namespace neat {
+namespace {
+
+// Counting sort of genomes by level count, deepest first (one block).
+__global__ void __launch_bounds__(1024) schedule_kernel(const uint8_t *rec, size_t stride, int pop, int32_t *order)
+{
+    __shared__ int hist[NEAT_MAX_NODES + 2];
+    for (int i = threadIdx.x; i < NEAT_MAX_NODES + 2; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < pop; g += blockDim.x) {
+        const int lv = min((int)(__ldg(reinterpret_cast<const uint32_t *>(rec + (size_t)g * stride)) >> 16),
+                           NEAT_MAX_NODES);
+        atomicAdd(&hist[NEAT_MAX_NODES - lv], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {                 // exclusive scan (deepest bin first)
+        int run = 0;
+        for (int i = 0; i < NEAT_MAX_NODES + 1; ++i) {
+            const int c = hist[i];
+            hist[i] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < pop; g += blockDim.x) {
+        const int lv = min((int)(__ldg(reinterpret_cast<const uint32_t *>(rec + (size_t)g * stride)) >> 16),
+                           NEAT_MAX_NODES);
+        order[atomicAdd(&hist[NEAT_MAX_NODES - lv], 1)] = g;
+    }
+}
+
+}  // namespace
+}  // namespace neat
+
+extern "C" int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims d, int32_t *order_dev, void *stream)
+{
+    clear_error();
+    if (!dims_ok(d)) return invalid("neat_schedule: invalid dims");
+    if (pop < 0) return invalid("neat_schedule: pop < 0");
+    if (pop == 0) return NEAT_OK;
+    if (!transformed_dev || !order_dev) return invalid("neat_schedule: null pointer");
+    schedule_kernel<<<1, 1024, 0, as_stream(stream)>>>(static_cast<const uint8_t *>(transformed_dev),
+                                                       record_stride(d), pop, order_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_schedule: launch");
     return NEAT_OK;
 }

@@ -59,6 +59,7 @@ struct ForwardArgs {
     int rec_words;           // 16-byte words of shared memory reserved for a record
     int val_floats;          // floats of shared memory for node values (N * tile, rounded to 4)
     int rec_copy_bytes;      // bytes of each record copied in one piece (0: read the size from its header)
+    const int32_t *order;    // genome of work item k / tiles (NULL: identity)
 };
 
 // 16-byte words before the groups' regions in a forward block's shared

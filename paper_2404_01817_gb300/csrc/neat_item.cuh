@@ -68,6 +68,7 @@ __device__ __forceinline__ float partials(uint32_t agg, const uint2 *__restrict_
     if (nk == 4) {
         float q0 = id, q1 = id, q2 = id, q3 = id;
         uint32_t i = 0;
+#pragma unroll 2
         for (; i + 4 <= ec; i += 4) {
             const uint2 t0 = e[i], t1 = e[i + 1], t2 = e[i + 2], t3 = e[i + 3];
             q0 = agg_step(agg, q0, __uint_as_float(t0.x), v[vslot<T1>(t0.y, lgT, col)]);
@@ -141,10 +142,36 @@ __device__ __forceinline__ void walk_levels(const uint4 *srec, float *v, int G, 
     const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
     const uint16_t *lev = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.z);
     if (T1) {
-        // threads per node chosen per level: 4 when the level has at most
-        // G/4 nodes, 2 when at most G/2, else 1 (capped by lg_split_max);
         // the leading input positions of level 0 are skipped
         int p0 = (int)(h0.w >> 16);
+        if (lg_split_max == 0) {                 // one thread per node, no shuffles
+            // the node entry of a thread's first node in the next level is
+            // read before the level barrier (entries do not depend on values)
+            int p1 = lev[1];
+            uint4 ne = (p0 + lane < n_nodes) ? nodes[p0 + lane] : make_uint4(0u, 0u, 0u, (uint32_t)kInputAct);
+            for (int l = 0; l < n_levels; ++l) {
+                const int p2 = lev[l + 2 <= n_levels ? l + 2 : n_levels];
+                for (int p = p0 + lane; p < p1; p += G) {
+                    if (p != p0 + lane) ne = nodes[p];
+                    const uint32_t act = ne.w & 0xffu;
+                    if (act == kInputAct) continue;
+                    const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
+                    const uint32_t ec = ne.z >> 16;
+                    const float a = partials<true, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, 0, 0, 0, 4);
+                    v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                                : node_output(ne, agg, act, ec, a);
+                }
+                const int pn = p1 + lane;
+                if (pn < n_nodes) ne = nodes[pn];
+                p0 = p1;
+                p1 = p2;
+                group_sync(G, gi);
+            }
+            group_sync(G, gi);
+            return;
+        }
+        // threads per node chosen per level: 4 when the level has at most
+        // G/4 nodes, 2 when at most G/2, else 1 (capped by lg_split_max)
         for (int l = 0; l < n_levels; ++l) {
             const int p1 = lev[l + 1];
             const int cnt = p1 - p0;

@@ -537,7 +537,18 @@ extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const 
             b.max_used = std::max<int>(b.max_used, (int)align16(used));
         }
     }
-    for (HostBucket &b : P->hb) b.shape = heuristic_shape(b.n_class, P->pops[b.pop_index].batch);
+    // within a bucket, deepest and largest genomes first: groups that share
+    // a warp then have similar level counts (a warp walks as many levels as
+    // its deepest genome), and the longest items start first
+    for (HostBucket &b : P->hb) {
+        const std::vector<uint32_t> &h = hdrs[b.pop_index];
+        std::stable_sort(b.gidx.begin(), b.gidx.end(), [&](int32_t x, int32_t y) {
+            const uint32_t lx = h[(size_t)x * 8] >> 16, ly = h[(size_t)y * 8] >> 16;
+            if (lx != ly) return lx > ly;
+            return h[(size_t)x * 8 + 1] > h[(size_t)y * 8 + 1];
+        });
+        b.shape = heuristic_shape(b.n_class, P->pops[b.pop_index].batch);
+    }
     size_t total = 0;
     for (const HostBucket &b : P->hb) total += b.gidx.size();
     if (total > 0) {

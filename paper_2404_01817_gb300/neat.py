@@ -36,10 +36,11 @@ class Dims(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("groups_per_block", ctypes.c_int32), ("pdl", ctypes.c_int32), ("split", ctypes.c_int32)]
+                ("groups_per_block", ctypes.c_int32), ("pdl", ctypes.c_int32), ("split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("order_dev", ctypes.c_void_p)]
 
-    def __init__(self, group=8, tile=1, groups_per_block=1, pdl=0, split=1):
-        super().__init__(group, tile, groups_per_block, pdl, split)
+    def __init__(self, group=8, tile=1, groups_per_block=1, pdl=0, split=1, order=None):
+        super().__init__(group, tile, groups_per_block, pdl, split, 0, None if order is None else order.data_ptr())
 
     def __repr__(self):
         return (f"Launch(group={self.group}, tile={self.tile}, groups_per_block={self.groups_per_block}, "
@@ -96,6 +97,7 @@ _sig = {
     "neat_forward": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, _P]),
     "neat_default_launch": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
     "neat_device_error": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_uint32)]),
+    "neat_schedule": (ctypes.c_int, [_P, _i32, Dims, _P, _P]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
@@ -171,6 +173,15 @@ def neat_default_launch(pop: int, d: Dims, batch: int) -> Launch:
     L = Launch()
     _check(_lib.neat_default_launch(pop, d, batch, ctypes.byref(L)), "neat_default_launch")
     return L
+
+
+def neat_schedule(transformed, pop: int, d: Dims, order=None, stream=None):
+    """Depth-descending genome order (int32 [pop], device) for Launch(order=...)."""
+    import torch
+    if order is None:
+        order = torch.empty(max(pop, 1), dtype=torch.int32, device=transformed.device)
+    _check(_lib.neat_schedule(_ptr(transformed), pop, d, _ptr(order), _stream(stream)), "neat_schedule")
+    return order[:pop]
 
 
 def neat_device_error(clear: bool = True) -> int:

@@ -261,3 +261,34 @@ def test_ant_full_size_sampled_steps(neat):
         worst = max(worst, mscaled)
     cache.close()
     print(f"ant full-size max scaled error {worst:.3g}")
+
+
+def test_schedule_order_is_a_permutation_and_changes_nothing(neat):
+    import torch
+    for pop, B in [(W.ant_population(8, 2000), 1), (W.batched_populations(8, pop=100)[3], 16)]:
+        d, rec = _check_transform(neat, pop, "schedule")
+        order = neat.neat_schedule(rec, pop.pop, d)
+        torch.cuda.synchronize()
+        o = order.cpu().numpy()
+        assert sorted(o.tolist()) == list(range(pop.pop))
+        dec = _decode(neat, rec, pop.pop, d)
+        assert np.all(np.diff(dec.n_levels[o]) <= 0)            # deepest first
+        x = _dev(W.normal_inputs(9, (pop.pop, B, pop.num_inputs)))
+        L0 = neat.neat_default_launch(pop.pop, d, B)
+        y0 = neat.neat_forward(rec, pop.pop, d, x, launch=L0).cpu().numpy()
+        L1 = neat.neat_default_launch(pop.pop, d, B)
+        L1.order_dev = order.data_ptr()
+        y1 = neat.neat_forward(rec, pop.pop, d, x, launch=L1).cpu().numpy()
+        np.testing.assert_array_equal(y0, y1)
+        if B == 1:
+            S = 4
+            xs = _dev(W.normal_inputs(10, (S, pop.pop, 1, pop.num_inputs)))
+            ys = torch.empty((S, pop.pop, 1, pop.num_outputs), device="cuda")
+            L1.pdl = 1
+            cache = neat.StepsCache()
+            neat.neat_forward_steps(rec, pop.pop, d, xs, ys, cache, launch=L1)
+            torch.cuda.synchronize()
+            for s in range(S):
+                np.testing.assert_array_equal(ys[s].cpu().numpy(),
+                                              neat.neat_forward(rec, pop.pop, d, xs[s].contiguous()).cpu().numpy())
+            cache.close()
