@@ -557,7 +557,7 @@ def main():
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
-    for fn in ("neat_forward.cu", "neat_device.cuh", "neat_internal.h"):
+    for fn in ("neat_forward.cu", "neat_device.cuh", "neat_internal.h", "neat_item.cuh"):
         with open(os.path.join(ROOT, "paper_2404_01817_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

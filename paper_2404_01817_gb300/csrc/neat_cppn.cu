@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     }
     const int n_nodes = (int)(h0.x & 0xffffu);
     const int first = (int)(h0.w >> 16);               // leading input positions need no evaluation
+    const bool sum_only = ((h0.w >> 8) & 0xffu) == 0u;  // uniform sum aggregation
     const uint4 *nodes = srec + 2;
     const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
     const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
@@ -96,7 +97,10 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
         v[(pin2 << lgT) + tid] = coord[t % a.res];
         v[(pin3 << lgT) + tid] = coord[t / a.res];
         v[(pin4 << lgT) + tid] = 1.0f;
-        for (int p = first; p < n_nodes; ++p) eval_node<false, false>(nodes[p], edges, v, p, lgT, tid);
+        if (sum_only)
+            for (int p = first; p < n_nodes; ++p) eval_node_sum<false>(nodes[p], edges, v, p, lgT, tid);
+        else
+            for (int p = first; p < n_nodes; ++p) eval_node<false, false>(nodes[p], edges, v, p, lgT, tid);
         const float w = v[(pout << lgT) + tid];
         out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
     }

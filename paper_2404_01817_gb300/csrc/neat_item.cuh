@@ -123,6 +123,19 @@ __device__ __forceinline__ void eval_node(const uint4 ne, const uint2 *__restric
                                      : node_output(ne, agg, act, ec, a);
 }
 
+// One whole node for one column when every non-input node of the genome
+// aggregates by sum (any activation): no aggregation dispatch.
+template <bool T1>
+__device__ __forceinline__ void eval_node_sum(const uint4 ne, const uint2 *__restrict__ edges,
+                                              float *__restrict__ v, int p, int lgT, int col)
+{
+    const uint32_t act = ne.w & 0xffu;
+    if (act == kInputAct) return;
+    const uint32_t ec = ne.z >> 16;
+    const float a = partials<T1, true>(kAggSum, edges + (ne.z & 0xffffu), ec, v, lgT, col, 0, 4);
+    v[vslot<T1>(p, lgT, col)] = activate(act, fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)));
+}
+
 // All non-input nodes of a staged record, for the columns this thread owns.
 //  Columns (T > 1): thread `lane` = (sub, col) computes column col of nodes
 //  sub, sub + nsub, ... of every level, nsub = G / T.
