@@ -57,8 +57,8 @@ def parse():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
-            int(os.environ.get("WORLD_SIZE", 1)))
+    from paper_2404_01817_gb300.shard import rank_env
+    return rank_env()
 
 
 class ClockSampler:
@@ -208,7 +208,7 @@ def run_batched(args):
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
     dev = torch.device("cuda", 0)
-    S, B = 100, 64
+    S, B = (2 if args.profile else 100), 64
     pops = W.batched_populations(0, pop=2048)
     descs = []
     for j, p in enumerate(pops):
@@ -221,6 +221,16 @@ def run_batched(args):
         descs.append(dict(transformed=rec, pop=p.pop, dims=d, inputs=x, outputs=y))
     stream = torch.cuda.current_stream(dev)
     plan = neat.Plan(descs, autotune=True)
+    if args.profile:                       # one step inside an NVTX range, for ncu --nvtx-include neat_step/
+        plan.forward(0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("neat_step")
+        plan.forward(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps(plan.describe()), flush=True)
+        plan.close()
+        return
     for _ in range(args.warmup):
         plan.forward_steps(0, S)
     torch.cuda.synchronize()
@@ -379,7 +389,8 @@ def main():
     from paper_2404_01817_gb300 import workloads as W
 
     S = args.env_steps
-    pop = W.ant_population(rank, POP)          # each rank evaluates its own population
+    from paper_2404_01817_gb300.shard import job_throughput, max_over_ranks, population_seed
+    pop = W.ant_population(population_seed(rank), POP)     # each rank evaluates its own population
     d = neat.dims(I, O, NMAX, CMAX)
     nodes = torch.from_numpy(pop.nodes).to(dev)
     conns = torch.from_numpy(pop.conns).to(dev)
@@ -417,22 +428,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def reduce_max(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    if args.profile:
-        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
-        neat.neat_schedule(rec, POP, d, order, stream=stream)
-        for s in range(3):
-            neat.neat_forward(rec, POP, d, obs[s], act[s], launch=L_plain, stream=stream)
-        neat.neat_forward_steps(rec, POP, d, obs[:8], act[:8], cache, launch=L_batched, stream=stream)
-        torch.cuda.synchronize(dev)
-        cache.close()
-        print("profile case done", flush=True)
-        return
+        return max_over_ranks(x, dev)
 
     # ---- warm-up (also builds the CUDA graph)
     for _ in range(args.warmup):
@@ -463,7 +459,7 @@ def main():
     t_batched = reduce_max(ev0.elapsed_time(ev1) / 1e3)
     ep_ms = [a.elapsed_time(b) for a, b in ep_events]
     fw_ms = [a.elapsed_time(b) for a, b in fw_events]
-    value = world * POP * S * args.steps / t_batched
+    value = job_throughput(POP * S * args.steps, world, t_batched)
 
     # ---- plain: one launch per step from the host, per-step latency
     n_plain = max(1, min(args.steps, 5))

@@ -438,6 +438,16 @@ NEAT_API void neat_serve_destroy(neat_server *srv);
 /* The serving observations: count N(0,1) floats of (seed, step) into out_dev. */
 NEAT_API int neat_fill_normal(uint64_t seed, int32_t step, int64_t count, float *out_dev, void *stream);
 
+/*
+ * Failure-detection self-test (synchronous): one GPU thread waits on an
+ * mbarrier phase that never completes, with a bound of limit_us
+ * microseconds.  The wait gives up, bit 0 of the device error word is set
+ * (see neat_device_error) and the kernel returns; *result_host = 2.  (1 would
+ * mean the phase completed, which cannot happen.)  No fault, no hang: the
+ * context stays usable.
+ */
+NEAT_API int neat_selftest_bounded_wait(uint32_t limit_us, uint32_t *result_host);
+
 /* Description of the last error on this thread ("" if none). */
 NEAT_API const char *neat_last_error(void);
 

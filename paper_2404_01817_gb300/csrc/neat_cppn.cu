@@ -35,6 +35,7 @@ struct CppnArgs {
     int chunks;              // blocks per genome
     float threshold;
     int rec_words;           // 16-byte words of the record region
+    int use_xy;              // node coordinate table in shared memory (res^2 <= 4096)
 };
 
 __device__ unsigned int g_cppn_error;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     const long q0 = (long)(blockIdx.x - (long)g * a.chunks) * (kCppnThreads * kCppnQueriesPerThread);
     uint4 *srec = smem;
     float *v = reinterpret_cast<float *>(smem + a.rec_words);
+    float2 *nodexy = reinterpret_cast<float2 *>(v + (size_t)a.N * kCppnThreads);   // (x, y) of node i
     const uint32_t bar = smem_addr(&bar_mem);
     const uint8_t *grec = a.rec + (size_t)g * a.stride;
     if (tid == 0) {
@@ -61,6 +63,8 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     for (int i = tid; i < a.res; i += kCppnThreads)
         coord[i] = (float)(-1.0 + 2.0 * (double)i / (double)(a.res - 1));
     __syncthreads();
+    if (a.use_xy)
+        for (int i = tid; i < a.res * a.res; i += kCppnThreads) nodexy[i] = make_float2(coord[i % a.res], coord[i / a.res]);
     __shared__ int failed;
     if (tid == 0) failed = 0;
     __syncthreads();
@@ -85,17 +89,28 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     const uint4 *nodes = srec + 2;
     const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
     const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
-    const int lgT = ilog2(kCppnThreads);
+    constexpr int lgT = 8;                              // log2(kCppnThreads): value slot = (p << 8) + tid
+    static_assert((1 << lgT) == kCppnThreads, "tile of the CPPN value array");
     const int pin0 = io[0], pin1 = io[1], pin2 = io[2], pin3 = io[3], pin4 = io[4], pout = io[5];
-    const long per_block = (long)a.res * a.res * a.res * a.res;
+    const int per_block = a.res * a.res * a.res * a.res;
     const int rr = a.res * a.res;
+    // (source, target) of this thread's first query; later queries advance
+    // it by kCppnThreads without dividing
+    int r = (int)((q0 + tid) % per_block);
+    int s = r / rr, t = r - s * rr;
     for (long q = q0 + tid; q < qend; q += kCppnThreads) {
-        const int r = (int)(q % per_block);
-        const int s = r / rr, t = r - s * rr;
-        v[(pin0 << lgT) + tid] = coord[s % a.res];
-        v[(pin1 << lgT) + tid] = coord[s / a.res];
-        v[(pin2 << lgT) + tid] = coord[t % a.res];
-        v[(pin3 << lgT) + tid] = coord[t / a.res];
+        float2 ps, pt;
+        if (a.use_xy) {
+            ps = nodexy[s];
+            pt = nodexy[t];
+        } else {
+            ps = make_float2(coord[s % a.res], coord[s / a.res]);
+            pt = make_float2(coord[t % a.res], coord[t / a.res]);
+        }
+        v[(pin0 << lgT) + tid] = ps.x;
+        v[(pin1 << lgT) + tid] = ps.y;
+        v[(pin2 << lgT) + tid] = pt.x;
+        v[(pin3 << lgT) + tid] = pt.y;
         v[(pin4 << lgT) + tid] = 1.0f;
         if (sum_only)
             for (int p = first; p < n_nodes; ++p) eval_node_sum<false>(nodes[p], edges, v, p, lgT, tid);
@@ -103,6 +118,18 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
             for (int p = first; p < n_nodes; ++p) eval_node<false, false>(nodes[p], edges, v, p, lgT, tid);
         const float w = v[(pout << lgT) + tid];
         out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
+        r += kCppnThreads;
+        t += kCppnThreads;
+        if (r >= per_block) {                          // into the next layer block
+            r -= per_block;
+            s = r / rr;
+            t = r - s * rr;
+        } else {
+            while (t >= rr) {
+                t -= rr;
+                ++s;
+            }
+        }
     }
 }
 
@@ -139,7 +166,9 @@ extern "C" int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_di
     a.chunks = (int)((a.queries + per_block - 1) / per_block);
     a.threshold = threshold;
     a.rec_words = (int)(record_max_bytes(5, 1, d.max_nodes, d.max_conns) / 16);
-    const size_t smem = (size_t)a.rec_words * 16 + 4u * (size_t)d.max_nodes * kCppnThreads;
+    a.use_xy = (r2 <= 4096) ? 1 : 0;
+    const size_t smem = (size_t)a.rec_words * 16 + 4u * (size_t)d.max_nodes * kCppnThreads +
+                        (a.use_xy ? 8u * (size_t)r2 : 0u);
     if (smem > 200u * 1024u) return invalid("neat_cppn_query: genome too large for one block (max_nodes <= 160)");
     const long blocks = (long)pop * a.chunks;
     if (blocks > 0x7fffffffL) return invalid("neat_cppn_query: too many queries");

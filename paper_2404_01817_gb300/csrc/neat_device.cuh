@@ -76,7 +76,7 @@ __device__ __forceinline__ uint64_t global_ns()
 // the thread for up to kWaitHintNs instead of spinning.
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
 constexpr uint32_t kWaitHintNs = 2000;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t phase, uint64_t limit_ns)
 {
     uint64_t t0 = 0;
     for (uint32_t i = 0;; ++i) {
@@ -87,10 +87,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
         if ((i & 63u) == 0) {
             const uint64_t t = global_ns();
             if (i == 0) t0 = t;
-            else if (t - t0 > kWaitLimitNs) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
 }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) { return mbar_wait_for(bar, phase, kWaitLimitNs); }
 
 // Order earlier generic-proxy accesses of shared memory before later
 // async-proxy (bulk copy) writes to it.

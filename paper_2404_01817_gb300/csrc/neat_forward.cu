@@ -581,3 +581,45 @@ extern "C" int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims
     if (e != cudaSuccess) return cuda_fail(e, "neat_schedule: launch");
     return NEAT_OK;
 }
+
+// ------------------------------------------------ bounded-wait self-test
+
+namespace neat {
+namespace {
+
+// One thread waits on an mbarrier that expects two arrivals but gets one:
+// the phase never completes, the bounded wait gives up after limit_ns, the
+// error word gets kErrWaitExpired and the kernel returns normally.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned int *result)
+{
+    __shared__ uint64_t bar_mem;
+    const uint32_t bar = smem_addr(&bar_mem);
+    mbar_init(bar, 2);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    const bool ok = mbar_wait_for(bar, 0, limit_ns);
+    if (!ok) atomicOr(&g_forward_error, kErrWaitExpired);
+    *result = ok ? 1u : 2u;
+    mbar_inval(bar);
+}
+
+}  // namespace
+}  // namespace neat
+
+extern "C" int neat_selftest_bounded_wait(uint32_t limit_us, uint32_t *result_host)
+{
+    clear_error();
+    if (!result_host) return invalid("neat_selftest_bounded_wait: null pointer");
+    if (limit_us == 0 || limit_us > 2000000u) return invalid("neat_selftest_bounded_wait: limit in 1..2000000 us");
+    unsigned int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "neat_selftest_bounded_wait: cudaMalloc");
+    selftest_wait_kernel<<<1, 1>>>((uint64_t)limit_us * 1000ull, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned int r = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&r, d, sizeof(r), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_selftest_bounded_wait");
+    *result_host = r;
+    return NEAT_OK;
+}

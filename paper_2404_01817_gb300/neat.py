@@ -98,6 +98,7 @@ _sig = {
     "neat_default_launch": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
     "neat_device_error": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_schedule": (ctypes.c_int, [_P, _i32, Dims, _P, _P]),
+    "neat_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
@@ -182,6 +183,12 @@ def neat_schedule(transformed, pop: int, d: Dims, order=None, stream=None):
         order = torch.empty(max(pop, 1), dtype=torch.int32, device=transformed.device)
     _check(_lib.neat_schedule(_ptr(transformed), pop, d, _ptr(order), _stream(stream)), "neat_schedule")
     return order[:pop]
+
+
+def neat_selftest_bounded_wait(limit_us: int = 20000) -> int:
+    r = ctypes.c_uint32(0)
+    _check(_lib.neat_selftest_bounded_wait(limit_us, ctypes.byref(r)), "neat_selftest_bounded_wait")
+    return r.value
 
 
 def neat_device_error(clear: bool = True) -> int:
