@@ -149,20 +149,28 @@ def cpu_baseline(pop, obs_host, seconds_target=15.0):
                       f"transform once per genome + forward per step, {cores} threads)"}
 
 
+WORKLOAD = ("Ant-shaped control: 10000 genomes/GPU, 27 in / 8 out, max 50 nodes / 200 conns, "
+            "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + "
+            "1000 sequential forwards (1 obs/genome/step)")
+
+
 def run_reference(args):
-    """The oracle as the reference arm: bounded samples of the same workload."""
+    """The reference arm: the FP64 oracle (the paper ships no code) on the
+    same workload, all host cores.  One bench step = one episode of the
+    workload (every genome transformed once and evaluated on its 1000
+    observations), rank 0 only."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    from paper_2404_01817_gb300 import workloads as W
-    pop = W.ant_population(0, POP)
-    obs = W.normal_inputs(0, (60, POP, 1, I))
-    import oracle
-    xs = np.ascontiguousarray(obs[:, :, 0, :].transpose(1, 0, 2))
     import concurrent.futures as cf
+
+    import oracle
+    from paper_2404_01817_gb300 import workloads as W
+    S = args.env_steps
+    pop = W.ant_population(0, POP)
+    xs = W.normal_inputs(0, (POP, S, I))                 # [genome][step][input]
     cores = os.cpu_count() or 1
     chunks = np.array_split(np.arange(POP), cores * 4)
-    S = xs.shape[1]
 
     def episode():
         with cf.ThreadPoolExecutor(max_workers=cores) as ex:
@@ -178,11 +186,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "Ant-shaped control: 10000 genomes, 27 in / 8 out, "
-                                                        "max 50 nodes / 200 conns, tanh, sum",
-                                            "sample": f"{S} steps per bench step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"all {POP} genomes x {S} steps per bench step, FP64 C oracle"},
+                             "sample": f"all {POP} genomes x {S} steps per bench step (the whole episode), "
+                                       f"FP64 C oracle, {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -552,9 +559,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batched / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "Ant-shaped control: 10000 genomes/GPU, 27 in / 8 out, max 50 nodes / 200 conns, "
-                               "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + "
-                               f"{S} sequential forwards (1 obs/genome/step)",
+        "config": {"workload": WORKLOAD,
                    "l2": "inputs larger than L2 (1.08 GB of observations per bench step)",
                    "form": "batched: CUDA graph of the steps with programmatic dependent launch, genomes in "
                            "depth order (neat_schedule)",
