@@ -250,7 +250,11 @@ def test_ant_full_size_sampled_steps(neat):
     x = torch.randn((S, 10000, 1, 27), device="cuda", generator=gen)
     y = torch.empty((S, 10000, 1, 8), device="cuda")
     cache = neat.StepsCache()
-    neat.neat_forward_steps(rec, 10000, d, x, y, cache)
+    L = neat.neat_default_launch(10000, d, 1)       # the batched launch bench.py times
+    L.pdl = 1
+    order = neat.neat_schedule(rec, 10000, d)
+    L.order_dev = order.data_ptr()
+    neat.neat_forward_steps(rec, 10000, d, x, y, cache, launch=L)
     torch.cuda.synchronize()
     worst = 0.0
     for s in (0, 1, 499, 998, 999):

@@ -91,3 +91,25 @@ def test_plan_steps_graph(neat):
             np.testing.assert_array_equal(d["outputs"][s].cpu().numpy(), ref)
     assert neat.neat_device_error() == 0
     plan.close()
+
+
+def test_plan_full_size_uneven_batch_sampled(neat):
+    """The uneven-batch workload at full size (4 x 2048 genomes, 64 inputs
+    each) through the autotuned plan bench.py times; sampled genomes against
+    the oracle."""
+    import torch
+    pops = W.batched_populations(0, pop=2048)
+    descs = _setup(neat, pops, 64, seed=77)
+    plan = neat.Plan(descs, autotune=True)
+    plan.forward(0)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for j, (p, dsc) in enumerate(zip(pops, descs)):
+        idx = np.random.default_rng(j).choice(p.pop, 48, replace=False)
+        sub = p.subset(idx)
+        x = dsc["inputs"].cpu().numpy()[idx]
+        ref = oracle.forward(sub.nodes, sub.conns, sub.num_inputs, sub.num_outputs, x)
+        mabs, mscaled = assert_outputs_close(dsc["outputs"].cpu().numpy()[idx], ref, what=f"full Nmax={p.max_nodes}")
+        worst = max(worst, mscaled)
+    print(f"uneven batch full-size max scaled error {worst:.3g}")
+    plan.close()
