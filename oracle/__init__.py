@@ -41,7 +41,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_transform.argtypes = [P, P, i, i, i, i, i] + [P] * 10
         L.oracle_forward.argtypes = [P, P, i, i, i, i, i, P, i, P]
         L.oracle_cppn_query.argtypes = [P, P, i, i, i, i, ctypes.c_float, P, ctypes.c_long, P, P]
-        for f in (L.oracle_transform, L.oracle_forward, L.oracle_cppn_query):
+        L.oracle_forward_recurrent.argtypes = [P, P, i, i, i, i, i, P, i, i, P, P]
+        for f in (L.oracle_transform, L.oracle_forward, L.oracle_cppn_query, L.oracle_forward_recurrent):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -101,3 +102,18 @@ def cppn_query(nodes, conns, res: int, threshold: float, queries) -> tuple[np.nd
     lib().oracle_cppn_query(_ptr(nodes), _ptr(conns), P, N, C, res, float(threshold),
                             _ptr(q), q.shape[0], _ptr(raw), _ptr(w))
     return raw, w
+
+
+def forward_recurrent(nodes, conns, num_inputs: int, num_outputs: int, inputs, iterations: int):
+    """Recurrent networks: K synchronous iterations from zero (see
+    neat_oracle.c).  Returns (outputs double [P][B][O], status uint32 [P])."""
+    nodes, conns = _genome_arrays(nodes, conns)
+    P, N, C = nodes.shape[0], nodes.shape[1], conns.shape[1]
+    inputs = np.ascontiguousarray(inputs, dtype=np.float32)
+    assert inputs.shape[0] == P and inputs.shape[2] == num_inputs
+    B = inputs.shape[1]
+    out = np.empty((P, B, num_outputs), np.float64)
+    st = np.empty(P, np.uint32)
+    lib().oracle_forward_recurrent(_ptr(nodes), _ptr(conns), P, num_inputs, num_outputs, N, C,
+                                   _ptr(inputs), B, iterations, _ptr(out), _ptr(st))
+    return out, st

@@ -413,3 +413,156 @@ int oracle_cppn_query(const float *nodes, const float *conns, int P, int Nmax, i
     genome_free(&g);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Recurrent networks (Section 3.3 divides networks into feedforward and
+ * recurrent ones by the presence of cycles, and the hyperparameters carry a
+ * network_type; the paper gives no recurrent algorithm).  Reading, fixed
+ * here: enabled connections may form cycles, self-loops included; the input
+ * nodes hold their inputs; every other node starts at 0 and K synchronous
+ * iterations follow, each node's new value computed from the previous
+ * iterate of its sources by the same node rule:
+ *   v_k[n] = act_n(bias_n + response_n * agg_n(w_c v_{k-1}[src_c])).
+ * The outputs are v_K at the output keys.  The row checks and status bits
+ * are the feedforward ones except ORC_CYCLE, which cannot occur.
+ */
+typedef struct {
+    uint32_t status;
+    int n_nodes;
+    int *row_key;      /* [Nmax] */
+    int *in_ptr;       /* [Nmax+1] by row */
+    int *in_src;       /* [Cmax] source row */
+    double *in_w;      /* [Cmax] */
+    int *input_row, *output_row;
+} rnn_t;
+
+static void rnn_build(const float *nodes, const float *conns, int I, int O, int Nmax, int Cmax, rnn_t *g)
+{
+    uint32_t st = 0;
+    int n = 0;
+    keyrow_t *map = malloc(sizeof(keyrow_t) * (size_t)(Nmax > 0 ? Nmax : 1));
+    for (int r = 0; r < Nmax; r++) {
+        const float *nd = nodes + (size_t)r * 5;
+        g->row_key[r] = -1;
+        if (isnan(nd[0])) continue;
+        if (!is_key(nd[0])) { st |= ORC_BADKEY; continue; }
+        if (!is_enum(nd[3], 4) || !is_enum(nd[4], 7)) st |= ORC_BADENUM;
+        if (isnan(nd[1]) || isnan(nd[2])) st |= ORC_BADATTR;
+        g->row_key[r] = (int)nd[0];
+        map[n].key = (long)nd[0];
+        map[n].row = r;
+        n++;
+    }
+    qsort(map, (size_t)n, sizeof(keyrow_t), cmp_keyrow);
+    for (int i = 1; i < n; i++)
+        if (map[i].key == map[i - 1].key) st |= ORC_DUPKEY;
+    for (int j = 0; j < I; j++) {
+        g->input_row[j] = lookup(map, n, j);
+        if (g->input_row[j] < 0) st |= ORC_MISSING_IO;
+    }
+    for (int j = 0; j < O; j++) {
+        g->output_row[j] = lookup(map, n, I + j);
+        if (g->output_row[j] < 0) st |= ORC_MISSING_IO;
+    }
+    int *dst = malloc(sizeof(int) * (size_t)(Cmax > 0 ? Cmax : 1));
+    int *src = malloc(sizeof(int) * (size_t)(Cmax > 0 ? Cmax : 1));
+    pair_t *pairs = malloc(sizeof(pair_t) * (size_t)(Cmax > 0 ? Cmax : 1));
+    int npairs = 0;
+    for (int c = 0; c < Cmax; c++) {
+        const float *cn = conns + (size_t)c * 4;
+        src[c] = dst[c] = -1;
+        if (isnan(cn[0]) || isnan(cn[1]) || isnan(cn[2])) continue;
+        if (!is_key(cn[0]) || !is_key(cn[1])) { st |= ORC_BADKEY; continue; }
+        pairs[npairs].a = (long)cn[0];
+        pairs[npairs].b = (long)cn[1];
+        npairs++;
+        if (cn[2] == 0.0f) continue;
+        if (isnan(cn[3])) st |= ORC_BADATTR;
+        int s = lookup(map, n, (long)cn[0]), d = lookup(map, n, (long)cn[1]);
+        if (s < 0 || d < 0) { st |= ORC_DANGLING; continue; }
+        if ((long)cn[1] < I) { st |= ORC_INTO_INPUT; continue; }
+        src[c] = s;
+        dst[c] = d;
+    }
+    qsort(pairs, (size_t)npairs, sizeof(pair_t), cmp_pair);
+    for (int i = 1; i < npairs; i++)
+        if (pairs[i].a == pairs[i - 1].a && pairs[i].b == pairs[i - 1].b) st |= ORC_DUPCONN;
+    /* incoming lists by destination row, ascending connection row */
+    int e = 0;
+    for (int r = 0; r < Nmax; r++) {
+        g->in_ptr[r] = e;
+        for (int c = 0; c < Cmax; c++) {
+            if (dst[c] != r) continue;
+            g->in_src[e] = src[c];
+            g->in_w[e] = (double)conns[(size_t)c * 4 + 3];
+            e++;
+        }
+    }
+    g->in_ptr[Nmax] = e;
+    g->n_nodes = n;
+    g->status = st;
+    free(pairs); free(src); free(dst); free(map);
+}
+
+/* One input vector: K synchronous iterations; y[O]. */
+static void rnn_forward_one(const rnn_t *g, const float *nodes, int I, int O, int Nmax, int K,
+                            const float *x, double *v, double *vn, double *y)
+{
+    if (g->status & ORC_ERROR_MASK) {
+        for (int j = 0; j < O; j++) y[j] = NAN;
+        return;
+    }
+    for (int r = 0; r < Nmax; r++) v[r] = 0.0;
+    for (int j = 0; j < I; j++) v[g->input_row[j]] = (double)x[j];
+    for (int k = 0; k < K; k++) {
+        for (int r = 0; r < Nmax; r++) {
+            vn[r] = v[r];
+            if (g->row_key[r] < I) continue;       /* absent rows and inputs keep their value */
+            const float *nd = nodes + (size_t)r * 5;
+            int b = g->in_ptr[r], e = g->in_ptr[r + 1];
+            int agg = (int)nd[3];
+            double a = 0.0;
+            if (e > b) {
+                if (agg == 0 || agg == 3) {
+                    for (int i = b; i < e; i++) a = a + g->in_w[i] * v[g->in_src[i]];
+                    if (agg == 3) a = a / (double)(e - b);
+                } else if (agg == 1) {
+                    a = 1.0;
+                    for (int i = b; i < e; i++) a = a * (g->in_w[i] * v[g->in_src[i]]);
+                } else {
+                    a = g->in_w[b] * v[g->in_src[b]];
+                    for (int i = b + 1; i < e; i++) a = fmax(a, g->in_w[i] * v[g->in_src[i]]);
+                }
+            }
+            vn[r] = act_fn((int)nd[4], (double)nd[1] + (double)nd[2] * a);
+        }
+        double *t = v; v = vn; vn = t;
+    }
+    for (int j = 0; j < O; j++) y[j] = v[g->output_row[j]];
+}
+
+/* Recurrent forward of P genomes, B input vectors each, K iterations:
+ * inputs[P][B][I] -> out[P][B][O]; status[P] (may be NULL). */
+int oracle_forward_recurrent(const float *nodes, const float *conns, int P, int I, int O, int Nmax, int Cmax,
+                             const float *inputs, int B, int K, double *out, uint32_t *status)
+{
+    rnn_t g;
+    g.row_key = malloc(sizeof(int) * (size_t)Nmax);
+    g.in_ptr = malloc(sizeof(int) * (size_t)(Nmax + 1));
+    g.in_src = malloc(sizeof(int) * (size_t)(Cmax > 0 ? Cmax : 1));
+    g.in_w = malloc(sizeof(double) * (size_t)(Cmax > 0 ? Cmax : 1));
+    g.input_row = malloc(sizeof(int) * (size_t)(I > 0 ? I : 1));
+    g.output_row = malloc(sizeof(int) * (size_t)(O > 0 ? O : 1));
+    double *v = malloc(sizeof(double) * (size_t)Nmax), *vn = malloc(sizeof(double) * (size_t)Nmax);
+    for (int k = 0; k < P; k++) {
+        const float *nd = nodes + (size_t)k * Nmax * 5;
+        rnn_build(nd, conns + (size_t)k * Cmax * 4, I, O, Nmax, Cmax, &g);
+        if (status) status[k] = g.status;
+        for (int b = 0; b < B; b++)
+            rnn_forward_one(&g, nd, I, O, Nmax, K, inputs + ((size_t)k * B + b) * I, v, vn,
+                            out + ((size_t)k * B + b) * O);
+    }
+    free(v); free(vn);
+    free(g.row_key); free(g.in_ptr); free(g.in_src); free(g.in_w); free(g.input_row); free(g.output_row);
+    return 0;
+}

@@ -312,3 +312,48 @@ def request_population(req: dict) -> Population:
         hidden=lambda r: int(r.integers(0, max(nmax - I - O, 0) + 1)),
         edges=lambda r, n: int(r.integers(2 * n, 4 * n + 1)),
         acts=(ACT_TANH,), aggs=(AGG_SUM,), p_disabled=0.1, stream=6)
+
+
+def random_recurrent_population(seed: int, pop: int, num_inputs: int, num_outputs: int,
+                                max_nodes: int, max_conns: int,
+                                hidden: Callable[[np.random.Generator], int],
+                                edges: Callable[[np.random.Generator, int], int],
+                                acts: Sequence[int] = (ACT_TANH,), aggs: Sequence[int] = (AGG_SUM,),
+                                p_disabled: float = 0.1, stream: int = 20) -> Population:
+    """Recurrent genomes: connections drawn without duplicates among all
+    (source any node, destination any non-input node) pairs, so cycles and
+    self-loops occur; otherwise as random_dag_population."""
+    I, O = num_inputs, num_outputs
+    P = empty_population(pop, max_nodes, max_conns, I, O)
+    acts = np.asarray(acts, dtype=np.float32)
+    aggs = np.asarray(aggs, dtype=np.float32)
+    for g in range(pop):
+        rng = rng_for(seed, stream, g)
+        H = int(min(max(hidden(rng), 0), max_nodes - I - O))
+        n = I + O + H
+        m = O + H
+        nodes = P.nodes[g]
+        nodes[:n, 0] = np.arange(n, dtype=np.float32)
+        nodes[:n, 1] = rng.standard_normal(n).astype(np.float32)
+        nodes[:n, 2] = 1.0
+        nodes[:n, 3] = aggs[rng.integers(0, aggs.size, size=n)]
+        nodes[:n, 4] = acts[rng.integers(0, acts.size, size=n)]
+        total = n * m
+        E = int(min(edges(rng, n), max_conns, total))
+        picks = rng.choice(total, size=E, replace=False)
+        src = picks // m
+        dst = I + picks % m
+        conns = P.conns[g]
+        conns[:E, 0] = src
+        conns[:E, 1] = dst
+        conns[:E, 2] = (rng.random(E) >= p_disabled).astype(np.float32)
+        conns[:E, 3] = rng.standard_normal(E).astype(np.float32)
+    return P
+
+
+def ant_recurrent_population(seed: int = 0, pop: int = 10000) -> Population:
+    """Ant-shaped recurrent genomes (27 in, 8 out, max 50 nodes / 200 conns,
+    tanh, sum), connections in any direction."""
+    return random_recurrent_population(seed, pop, 27, 8, 50, 200,
+                                       hidden=lambda r: int(r.integers(0, 16)),
+                                       edges=lambda r, n: int(r.integers(100, 201)), stream=21)
