@@ -257,12 +257,52 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
 
 /*
- * Device error word of the forward, plan and CPPN kernels: bit 0 is set when a
+ * Device error word of the forward, plan, CPPN and recurrent kernels: bit 0 is set when a
  * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
  * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).
  */
 NEAT_API int neat_device_error(int32_t clear, uint32_t *out_host);
+
+/* ------------------------------------------------------ recurrent nets
+ *
+ * Networks whose enabled connections form cycles (Section 3.3 names
+ * recurrent networks beside feedforward ones; the paper gives no algorithm
+ * for them).  This library's definition: input nodes hold their inputs,
+ * every other node starts at 0, and `iterations` synchronous iterations
+ * follow, each computing every non-input node from the previous iterate:
+ *   v_k[n] = act_n(bias_n + response_n * agg_n(w_c v_{k-1}[src_c]))
+ * (same rule, ids and aggregation order as the feedforward path).  The
+ * outputs are the last iterate at the output keys.  On an acyclic genome,
+ * as many iterations as it has levels give the feedforward outputs.
+ */
+
+/* Transform for recurrent networks: the checks and record layout of
+ * neat_transform, but cycles (self-loops included) are allowed, there is no
+ * topological sort (positions follow node rows, one level) and
+ * NEAT_G_CYCLE is never set. */
+NEAT_API int neat_transform_recurrent(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                                      void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
+                                      void *stream);
+
+/* Recurrent forward on records from neat_transform_recurrent: inputs
+ * f32 [pop][batch][I] -> outputs f32 [pop][batch][O] after `iterations`
+ * (>= 0) synchronous iterations, default launch shape.  Errors as
+ * neat_forward, plus NEAT_EINVAL for iterations < 0. */
+NEAT_API int neat_forward_recurrent(const void *transformed_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                    int32_t batch, int32_t iterations, float *outputs_dev, void *stream);
+
+/* As neat_forward_recurrent with an explicit launch shape (NULL = the
+ * default).  Fields as for neat_forward_ex, with `split` = 1 (every node of
+ * an iteration is in flight at once, so nodes are not split); shared memory
+ * per group is the record plus two value tiles. */
+NEAT_API int neat_forward_recurrent_ex(const void *transformed_dev, int32_t pop, neat_dims d,
+                                       const float *inputs_dev, int32_t batch, int32_t iterations,
+                                       float *outputs_dev, const neat_launch *launch, void *stream);
+
+/* Default launch shape of the recurrent forward (host only; queries the
+ * current device once). */
+NEAT_API int neat_default_launch_recurrent(int32_t pop, neat_dims d, int32_t batch, neat_launch *out);
 
 /* ---------------------------------------------------------- CPPN query
  *

@@ -355,6 +355,13 @@ int choose_groups_per_block(long items, int group, size_t per_group, const Devic
 }  // namespace
 }  // namespace neat
 
+namespace neat {
+int groups_per_block_for(long items, int group, size_t per_group)
+{
+    return choose_groups_per_block(items, group, per_group, device_caps());
+}
+}  // namespace neat
+
 extern "C" int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat_launch *out)
 {
     if (!out) return invalid("neat_default_launch: null pointer");
@@ -524,11 +531,12 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
         e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
         if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
     }
-    unsigned int vp = 0, vc = 0;
+    unsigned int vp = 0, vc = 0, vr = 0;
     int rc = read_plan_error(&vp, clear);
     if (rc == NEAT_OK) rc = read_cppn_error(&vc, clear);
+    if (rc == NEAT_OK) rc = read_rnn_error(&vr, clear);
     if (rc) return rc;
-    *out_host = v | vp | vc;
+    *out_host = v | vp | vc | vr;
     return NEAT_OK;
 }
 

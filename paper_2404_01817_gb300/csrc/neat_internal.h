@@ -102,5 +102,10 @@ int launch_plan_table(const BucketDev *table_dev, int nb, int total_items, unsig
                       size_t smem_regions, int block_threads, cudaStream_t s);
 int read_plan_error(unsigned int *v, int clear);   // neat_plan.cu
 int read_cppn_error(unsigned int *v, int clear);   // neat_cppn.cu
+int read_rnn_error(unsigned int *v, int clear);    // neat_recurrent.cu
+// Groups per block that put `items` groups of `group` threads, each needing
+// `per_group` bytes of shared memory, in the fewest waves with the busiest SM
+// least loaded (neat_forward.cu).
+int groups_per_block_for(long items, int group, size_t per_group);
 
 }  // namespace neat

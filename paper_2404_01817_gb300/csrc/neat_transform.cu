@@ -28,6 +28,7 @@ struct TransformArgs {
     size_t stride;
     int pop, I, O, N, C;
     int Np2, Cp2;   // powers of two >= N and >= max(C, 1)
+    int recurrent;  // cycles allowed: no Kahn order, every present node in level 0 (row order)
 };
 
 __device__ __forceinline__ bool is_key(float k)
@@ -178,10 +179,10 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     // 3. layered Kahn: level 0 = present nodes without enabled incoming edges
     for (int r = tid; r < N; r += nt) {
         cnt[r] = indeg[r];
-        if (level[r] == -1 && indeg[r] == 0) level[r] = 0;
+        if (level[r] == -1 && (indeg[r] == 0 || a.recurrent)) level[r] = 0;
     }
     if (lst) atomicOr(&st, lst);
-    for (int L = 0;; ++L) {
+    for (int L = 0; !a.recurrent; ++L) {
         if (tid == 0) changed = 0;
         __syncthreads();
         for (int c = tid; c < C; c += nt) {
@@ -317,9 +318,9 @@ extern "C" size_t neat_transformed_bytes(int32_t pop, neat_dims d)
     return record_stride(d) * (size_t)pop;
 }
 
-extern "C" int neat_transform(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
-                              void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
-                              void *stream)
+static int transform_impl(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                          void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev, void *stream,
+                          int recurrent)
 {
     clear_error();
     if (!dims_ok(d)) return invalid("neat_transform: invalid dims");
@@ -346,6 +347,7 @@ extern "C" int neat_transform(const float *nodes_dev, const float *conns_dev, in
     a.C = d.max_conns;
     a.Np2 = next_pow2(a.N);
     a.Cp2 = next_pow2(a.C > 0 ? a.C : 1);
+    a.recurrent = recurrent;
     const size_t smem = transform_smem_bytes(a.N, a.C, a.I, a.O, a.Np2, a.Cp2);
     const int threads = (a.N <= 64 && a.C <= 512) ? 128 : (a.N <= 256 && a.C <= 2048 ? 256 : 512);
     static bool attr_set = false;
@@ -361,4 +363,18 @@ extern "C" int neat_transform(const float *nodes_dev, const float *conns_dev, in
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_transform: launch");
     return NEAT_OK;
+}
+
+extern "C" int neat_transform(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                              void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
+                              void *stream)
+{
+    return transform_impl(nodes_dev, conns_dev, pop, d, transformed_dev, transformed_bytes, status_dev, stream, 0);
+}
+
+extern "C" int neat_transform_recurrent(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                                        void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev,
+                                        void *stream)
+{
+    return transform_impl(nodes_dev, conns_dev, pop, d, transformed_dev, transformed_bytes, status_dev, stream, 1);
 }

@@ -98,6 +98,10 @@ _sig = {
     "neat_default_launch": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
     "neat_device_error": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_schedule": (ctypes.c_int, [_P, _i32, Dims, _P, _P]),
+    "neat_transform_recurrent": (ctypes.c_int, [_P, _P, _i32, Dims, _P, ctypes.c_size_t, _P, _P]),
+    "neat_forward_recurrent": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _i32, _P, _P]),
+    "neat_forward_recurrent_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _i32, _P, ctypes.POINTER(Launch), _P]),
+    "neat_default_launch_recurrent": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
     "neat_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
@@ -215,6 +219,43 @@ def neat_transform(nodes, conns, d: Dims, transformed=None, status=None, stream=
                                transformed.numel() * transformed.element_size(), _ptr(status),
                                _stream(stream)), "neat_transform")
     return transformed, status[:pop]
+
+
+def neat_transform_recurrent(nodes, conns, d: Dims, transformed=None, status=None, stream=None):
+    """Transform for recurrent networks (cycles allowed); as neat_transform."""
+    import torch
+    pop = nodes.shape[0]
+    assert nodes.is_cuda and conns.is_cuda and nodes.is_contiguous() and conns.is_contiguous()
+    nbytes = neat_transformed_bytes(pop, d)
+    if transformed is None:
+        transformed = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=nodes.device)
+    if status is None:
+        status = torch.empty(max(pop, 1), dtype=torch.int32, device=nodes.device)
+    _check(_lib.neat_transform_recurrent(_ptr(nodes), _ptr(conns), pop, d, _ptr(transformed),
+                                         transformed.numel() * transformed.element_size(), _ptr(status),
+                                         _stream(stream)), "neat_transform_recurrent")
+    return transformed, status[:pop]
+
+
+def neat_default_launch_recurrent(pop: int, d: Dims, batch: int) -> Launch:
+    L = Launch()
+    _check(_lib.neat_default_launch_recurrent(pop, d, batch, ctypes.byref(L)), "neat_default_launch_recurrent")
+    return L
+
+
+def neat_forward_recurrent(transformed, pop: int, d: Dims, inputs, iterations: int, outputs=None,
+                           launch: Launch | None = None, stream=None):
+    """Recurrent forward: f32 [P][B][O] after `iterations` synchronous iterations."""
+    import torch
+    assert inputs.dtype == torch.float32 and inputs.is_contiguous()
+    assert inputs.shape[0] == pop and inputs.shape[2] == d.num_inputs
+    batch = inputs.shape[1]
+    if outputs is None:
+        outputs = torch.empty((pop, batch, d.num_outputs), dtype=torch.float32, device=inputs.device)
+    _check(_lib.neat_forward_recurrent_ex(_ptr(transformed), pop, d, _ptr(inputs), batch, iterations, _ptr(outputs),
+                                          ctypes.byref(launch) if launch is not None else None, _stream(stream)),
+           "neat_forward_recurrent")
+    return outputs
 
 
 def neat_forward(transformed, pop: int, d: Dims, inputs, outputs=None, launch: Launch | None = None,

@@ -1,0 +1,251 @@
+"""Recurrent networks through the C ABI (neat_transform_recurrent,
+neat_forward_recurrent) against the FP64 recurrent oracle.
+
+Rule under test (Section 3.3 names recurrent networks beside feedforward
+ones without an algorithm; this library fixes one): inputs held, every other
+node starts at 0, K synchronous iterations of the node rule.
+
+Tolerance: the usual |gpu - ref| <= 1e-5 max(1, |ref|), plus a conditioning
+term for iterated maps.  A random recurrent map can be chaotic: rounding of
+one FP32 ulp inside an iteration grows geometrically with K, so the FP32 and
+FP64 iterates drift apart by an amount set by the dynamics, not by the
+kernel.  The oracle measures it itself: s = the change of its FP64 output when
+every bias moves by one float32 ulp (a perturbation of every pre-activation in
+every iteration, the size FP32 rounding injects); an output passes within
+1e-5 max(1, |ref|) + 64 s, and at least 99% of outputs must meet the plain
+bound.  Bounded activations run up to K = 25; populations with every
+activation and aggregation (identity, relu and product also grow in
+magnitude around a cycle) run at K <= 3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_01817_gb300 import workloads as W
+from tests.genome_helpers import genome, stack
+from tests.parity import TOL, assert_outputs_close, compare_outputs
+
+pytestmark = pytest.mark.gpu
+
+BOUNDED = (W.ACT_TANH, W.ACT_SIGMOID, W.ACT_SIN, W.ACT_GAUSS)
+
+
+@pytest.fixture(scope="module")
+def neat():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_01817_gb300 import neat as N
+    return N
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _dims(neat, pop):
+    return neat.dims(pop.num_inputs, pop.num_outputs, pop.max_nodes, pop.max_conns)
+
+
+def _run(neat, nodes, conns, I, O, x, K):
+    d = neat.dims(I, O, nodes.shape[1], conns.shape[1])
+    rec, st = neat.neat_transform_recurrent(_dev(nodes), _dev(conns), d)
+    y = neat.neat_forward_recurrent(rec, nodes.shape[0], d, _dev(x), K)
+    return rec, st.cpu().numpy().astype(np.uint32), y.cpu().numpy()
+
+
+def _population(seed, pop=97, acts=BOUNDED, aggs=(W.AGG_SUM, W.AGG_MEAN, W.AGG_MAX)):
+    return W.random_recurrent_population(seed, pop, 4, 3, 40, 160, hidden=lambda r: int(r.integers(0, 26)),
+                                         edges=lambda r, n: int(r.integers(n, 4 * n)), acts=acts, aggs=aggs,
+                                         p_disabled=0.15)
+
+
+def _bias_sensitivity(nodes, conns, I, O, x, K, ref):
+    """|change| of the oracle's outputs when every bias moves one float32 ulp
+    (either direction, the larger)."""
+    s = np.zeros_like(ref)
+    for direction in (np.inf, -np.inf):
+        moved = nodes.copy()
+        moved[:, :, 1] = np.nextafter(nodes[:, :, 1], np.float32(direction))
+        y, _ = oracle.forward_recurrent(moved, conns, I, O, x, K)
+        s = np.maximum(s, np.abs(np.nan_to_num(y) - np.nan_to_num(ref)))
+    return s
+
+
+def _assert_close_conditioned(y, ref, nodes, conns, I, O, x, K, what):
+    bad_plain, _, _, n = compare_outputs(y, ref)
+    assert bad_plain <= 0.01 * n, f"{what}: {bad_plain} of {n} outputs outside the plain tolerance"
+    if bad_plain:
+        s = _bias_sensitivity(nodes, conns, I, O, x, K, ref)
+        fin = np.isfinite(ref)
+        err = np.abs(np.asarray(y, np.float64) - ref)
+        allowed = TOL * np.maximum(1.0, np.abs(ref)) + 64.0 * s
+        worst = np.argmax(np.where(fin, err - allowed, -np.inf))
+        assert (err[fin] <= allowed[fin]).all(), \
+            f"{what}: error {err.flat[worst]:.3g} > allowed {allowed.flat[worst]:.3g} (sensitivity {s.flat[worst]:.3g})"
+        assert (np.isnan(y) == np.isnan(ref)).all()
+
+
+def _expected_lists(nodes, conns, I):
+    """Incoming lists of one genome by the recurrent record's rules: positions
+    are the present rows in ascending order; a node's enabled connections
+    from present nodes, into non-input keys, in ascending connection row."""
+    rows = [r for r in range(nodes.shape[0]) if not np.isnan(nodes[r, 0])]
+    row_of = {int(nodes[r, 0]): r for r in rows}
+    lists = {r: [] for r in rows}
+    for c in range(conns.shape[0]):
+        a, b, en, w = conns[c]
+        if np.isnan(a) or en == 0 or int(b) < I or int(a) not in row_of or int(b) not in row_of:
+            continue
+        lists[row_of[int(b)]].append((row_of[int(a)], np.float32(w)))
+    return rows, lists
+
+
+def test_recurrent_transform_records(neat):
+    pop = _population(1, pop=64)
+    d = _dims(neat, pop)
+    rec, st = neat.neat_transform_recurrent(_dev(pop.nodes), _dev(pop.conns), d)
+    st = st.cpu().numpy().astype(np.uint32)
+    _, ref_st = oracle.forward_recurrent(pop.nodes, pop.conns, 4, 3, np.zeros((64, 1, 4), np.float32), 1)
+    np.testing.assert_array_equal(st, ref_st)
+    assert not (st & neat.G_CYCLE).any()
+    # the feedforward transform rejects most of these genomes as cyclic
+    _, st_ff = neat.neat_transform(_dev(pop.nodes), _dev(pop.conns), d)
+    assert (st_ff.cpu().numpy() & neat.G_CYCLE).sum() > 32
+    dec = neat.decode_records(rec.cpu().numpy(), 64, d)
+    for g in range(64):
+        rows, lists = _expected_lists(pop.nodes[g], pop.conns[g], 4)
+        n = len(rows)
+        assert dec.n_levels[g] == 1 and dec.n_nodes[g] == n
+        np.testing.assert_array_equal(dec.order[g, :n], rows)
+        np.testing.assert_array_equal(dec.level_ptr[g, :2], [0, n])
+        for p, r in enumerate(rows):
+            k0, k1 = dec.in_ptr[g, p], dec.in_ptr[g, p + 1]
+            got = [(int(dec.in_src[g, k]), dec.in_w[g, k]) for k in range(k0, k1)]
+            assert got == lists[r], (g, p)
+        assert dec.in_ptr[g, n] == dec.n_edges[g] == sum(len(v) for v in lists.values())
+
+
+@pytest.mark.parametrize("K", [0, 1, 4, 25])
+@pytest.mark.parametrize("batch", [1, 3, 8, 37])
+def test_recurrent_matches_oracle_bounded(neat, batch, K):
+    pop = _population(100 + batch)
+    x = W.normal_inputs(7 + batch, (pop.pop, batch, 4))
+    _, st, y = _run(neat, pop.nodes, pop.conns, 4, 3, x, K)
+    ref, ref_st = oracle.forward_recurrent(pop.nodes, pop.conns, 4, 3, x, K)
+    np.testing.assert_array_equal(st, ref_st)
+    _assert_close_conditioned(y, ref, pop.nodes, pop.conns, 4, 3, x, K, f"recurrent batch {batch} K {K}")
+    if K == 0:
+        assert (y == 0).all()                            # no iteration: every non-input node is still 0
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_recurrent_all_activations_and_aggregations(neat, K):
+    pop = _population(200 + K, pop=211, acts=W.ALL_ACTS, aggs=W.ALL_AGGS)
+    x = W.normal_inputs(300 + K, (pop.pop, 5, 4))
+    _, st, y = _run(neat, pop.nodes, pop.conns, 4, 3, x, K)
+    ref, ref_st = oracle.forward_recurrent(pop.nodes, pop.conns, 4, 3, x, K)
+    np.testing.assert_array_equal(st, ref_st)
+    assert_outputs_close(y, ref, what=f"recurrent all acts/aggs K {K}")
+
+
+@pytest.mark.parametrize("batch", [1, 6])
+def test_recurrent_on_dags_equals_feedforward_bit_for_bit(neat, batch):
+    """On an acyclic genome, as many iterations as levels give the
+    feedforward outputs: the same incoming lists in the same order."""
+    pop = W.random_dag_population(9, 150, 3, 2, 30, 90, hidden=lambda r: int(r.integers(0, 20)),
+                                  edges=lambda r, n: int(r.integers(n, 3 * n)), acts=W.ALL_ACTS,
+                                  aggs=W.ALL_AGGS, p_disabled=0.2)
+    d = _dims(neat, pop)
+    x = _dev(W.normal_inputs(10, (150, batch, 3)))
+    rec_ff, st_ff = neat.neat_transform(_dev(pop.nodes), _dev(pop.conns), d)
+    assert (st_ff.cpu().numpy() & 0xFF == 0).all()
+    K = int(neat.decode_records(rec_ff.cpu().numpy(), 150, d).n_levels.max())
+    y_ff = neat.neat_forward(rec_ff, 150, d, x).cpu().numpy()
+    rec_r, _ = neat.neat_transform_recurrent(_dev(pop.nodes), _dev(pop.conns), d)
+    y_r = neat.neat_forward_recurrent(rec_r, 150, d, x, K).cpu().numpy()
+    np.testing.assert_array_equal(y_r, y_ff)
+    y_r2 = neat.neat_forward_recurrent(rec_r, 150, d, x, K + 3).cpu().numpy()
+    np.testing.assert_array_equal(y_r2, y_ff)                # a fixed point from then on
+
+
+def test_recurrent_columns_match_single_column_launches(neat):
+    """A batch of 16 (16-column tiles) and 16 launches of batch 1 (one
+    column per group) give the same bits."""
+    pop = _population(400, pop=40, acts=W.ALL_ACTS, aggs=W.ALL_AGGS)
+    x = W.normal_inputs(401, (40, 16, 4))
+    _, _, y = _run(neat, pop.nodes, pop.conns, 4, 3, x, 6)
+    for b in range(16):
+        _, _, yb = _run(neat, pop.nodes, pop.conns, 4, 3, np.ascontiguousarray(x[:, b:b + 1]), 6)
+        np.testing.assert_array_equal(yb[:, 0], y[:, b])
+
+
+def test_recurrent_closed_forms(neat):
+    # linear self-loop: y_K = c (1 - a^K) / (1 - a), a = r w_s, c = b + r w_x x
+    b, r, wx, ws = 0.3, 0.9, 1.25, -0.6
+    nodes, conns = genome([(0, 0, 1, 0, 0), (1, b, r, 0, 0)], [(0, 1, 1, wx), (1, 1, 1, ws)])
+    f = lambda v: float(np.float32(v))  # noqa: E731
+    for K in (0, 1, 2, 7, 40):
+        _, st, y = _run(neat, nodes, conns, 1, 1, np.array([[[0.75]]], np.float32), K)
+        a = f(r) * f(ws)
+        c = f(b) + f(r) * f(wx) * 0.75
+        want = c * (1 - a ** K) / (1 - a)
+        assert st[0] == 0 and abs(y[0, 0, 0] - want) <= 1e-5 * max(1.0, abs(want)), (K, y[0, 0, 0], want)
+
+
+def test_recurrent_errors_and_empty_shapes(neat):
+    import torch
+    rows = [(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1), (2, -0.1, 1, 0, 2)]
+    cyc = [(0, 2, 1, 1.0), (2, 1, 1, 0.5), (1, 2, 1, -0.7), (2, 2, 1, 0.25), (1, 0, 1, 3.0)]
+    good = genome(rows + [None], cyc)
+    dup = genome(rows + [(2, 0, 1, 0, 1)], cyc)            # duplicate key: an error
+    nodes, conns = stack([good, dup, good])
+    x = np.ones((3, 2, 1), np.float32)
+    _, st, y = _run(neat, nodes, conns, 1, 1, x, 6)
+    ref, ref_st = oracle.forward_recurrent(nodes, conns, 1, 1, x, 6)
+    np.testing.assert_array_equal(st, ref_st)
+    assert st[0] & neat.W_INTO_INPUT and st[1] & neat.G_DUPKEY
+    assert np.isnan(y[1]).all() and np.isfinite(y[[0, 2]]).all()
+    assert_outputs_close(y, ref, what="errors")
+    d = neat.dims(1, 1, 4, 5)
+    rec, _ = neat.neat_transform_recurrent(_dev(nodes), _dev(conns), d)
+    out = neat.neat_forward_recurrent(rec, 3, d, torch.empty((3, 0, 1), device="cuda"), 4)
+    assert out.shape == (3, 0, 1)
+    out = neat.neat_forward_recurrent(rec, 0, d, torch.empty((0, 2, 1), device="cuda"), 4)
+    assert out.shape == (0, 2, 1)
+    with pytest.raises(neat.NeatError):
+        neat.neat_forward_recurrent(rec, 3, d, _dev(x), -1)
+
+
+def test_recurrent_ant_full_population(neat):
+    """Ant-shaped recurrent genomes (27 in, 8 out, 50 nodes, 200 connections,
+    tanh, sum), 10000 genomes, one observation each; every 23rd genome
+    against the oracle."""
+    pop = W.ant_recurrent_population(0, 10000)
+    x = W.normal_inputs(11, (10000, 1, 27))
+    _, st, y = _run(neat, pop.nodes, pop.conns, 27, 8, x, 8)
+    assert (st & 0xFF == 0).all() and np.isfinite(y).all()
+    idx = np.arange(0, 10000, 23)
+    sub = pop.subset(idx)
+    ref, ref_st = oracle.forward_recurrent(sub.nodes, sub.conns, 27, 8, x[idx], 8)
+    np.testing.assert_array_equal(st[idx], ref_st)
+    _assert_close_conditioned(y[idx], ref, sub.nodes, sub.conns, 27, 8, x[idx], 8, "ant recurrent")
+
+
+def test_recurrent_launch_shapes_bit_identical(neat):
+    """Every valid launch shape (group, tile, groups per block, PDL) gives the
+    same bits as the default launch."""
+    pop = _population(500, pop=120, acts=W.ALL_ACTS, aggs=W.ALL_AGGS)
+    d = _dims(neat, pop)
+    x = _dev(W.normal_inputs(501, (120, 5, 4)))
+    rec, _ = neat.neat_transform_recurrent(_dev(pop.nodes), _dev(pop.conns), d)
+    ref = neat.neat_forward_recurrent(rec, 120, d, x, 5).cpu().numpy()
+    n = 0
+    for G, T, gpb, pdl in [(4, 1, 16, 0), (8, 1, 3, 1), (16, 1, 8, 0), (32, 1, 5, 1), (64, 1, 2, 0), (128, 1, 3, 1),
+                           (8, 2, 10, 0), (16, 4, 4, 1), (32, 8, 6, 0), (64, 16, 1, 1), (32, 32, 2, 0)]:
+        L = neat.neat_default_launch_recurrent(120, d, 5)
+        L.group, L.tile, L.groups_per_block, L.pdl = G, T, gpb, pdl
+        y = neat.neat_forward_recurrent(rec, 120, d, x, 5, launch=L).cpu().numpy()
+        np.testing.assert_array_equal(y, ref, err_msg=f"G={G} tile={T} gpb={gpb} pdl={pdl}")
+        n += 1
+    assert n == 11
