@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may use this package; the library's product path
 never does.  It imports nothing from the CUDA package and shares no code with
-it.  ``neat_oracle.c`` is the oracle proper (transform + forward + CPPN query
-in double, Section 3.3); ``definitional.py`` is a second, sort-free evaluator
+it.  ``neat_oracle.c`` is the oracle proper (transform + forward + CPPN query,
+recurrent forward and genome distance, in double); ``definitional.py`` is a second, sort-free evaluator
 used only to check it.
 """
 from __future__ import annotations
@@ -42,7 +42,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_forward.argtypes = [P, P, i, i, i, i, i, P, i, P]
         L.oracle_cppn_query.argtypes = [P, P, i, i, i, i, ctypes.c_float, P, ctypes.c_long, P, P]
         L.oracle_forward_recurrent.argtypes = [P, P, i, i, i, i, i, P, i, i, P, P]
-        for f in (L.oracle_transform, L.oracle_forward, L.oracle_cppn_query, L.oracle_forward_recurrent):
+        L.oracle_distance.argtypes = [P, P, i, P, P, i, i, i, ctypes.c_double, ctypes.c_double, P, P, P]
+        for f in (L.oracle_transform, L.oracle_forward, L.oracle_cppn_query, L.oracle_forward_recurrent,
+                  L.oracle_distance):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -117,3 +119,34 @@ def forward_recurrent(nodes, conns, num_inputs: int, num_outputs: int, inputs, i
     lib().oracle_forward_recurrent(_ptr(nodes), _ptr(conns), P, num_inputs, num_outputs, N, C,
                                    _ptr(inputs), B, iterations, _ptr(out), _ptr(st))
     return out, st
+
+
+def distance(nodes_a, conns_a, nodes_b, conns_b, c_disjoint: float, c_homologous: float):
+    """Genome distances (see neat_oracle.c): double [PA][PB], NaN where either
+    genome's homology is undefined; with the status words of both sides."""
+    nodes_a, conns_a = _genome_arrays(nodes_a, conns_a)
+    nodes_b, conns_b = _genome_arrays(nodes_b, conns_b)
+    assert nodes_a.shape[1:] == nodes_b.shape[1:] and conns_a.shape[1:] == conns_b.shape[1:]
+    PA, PB, N, C = nodes_a.shape[0], nodes_b.shape[0], nodes_a.shape[1], conns_a.shape[1]
+    out = np.empty((PA, PB), np.float64)
+    sa, sb = np.empty(PA, np.uint32), np.empty(PB, np.uint32)
+    lib().oracle_distance(_ptr(nodes_a), _ptr(conns_a), PA, _ptr(nodes_b), _ptr(conns_b), PB, N, C,
+                          float(c_disjoint), float(c_homologous), _ptr(out), _ptr(sa), _ptr(sb))
+    return out, sa, sb
+
+
+def speciate(distances, threshold: float) -> np.ndarray:
+    """Species of each genome (Algorithm 1, dividing the population by
+    distance): the representative (column) nearest to it among those closer
+    than the threshold, the lowest column on ties; -1 when none is.  NaN
+    distances never qualify."""
+    d = np.asarray(distances, np.float64)
+    out = np.full(d.shape[0], -1, np.int32)
+    for g in range(d.shape[0]):
+        best = None
+        for s in range(d.shape[1]):
+            if d[g, s] < threshold and (best is None or d[g, s] < d[g, best]):
+                best = s
+        if best is not None:
+            out[g] = best
+    return out

@@ -566,3 +566,116 @@ int oracle_forward_recurrent(const float *nodes, const float *conns, int P, int 
     free(g.row_key); free(g.in_ptr); free(g.in_src); free(g.in_w); free(g.input_row); free(g.output_row);
     return 0;
 }
+
+/*
+ * Genome distance for speciation.  Algorithm 1 divides the population into
+ * species by distances between networks; the hyperparameters name a weight
+ * for disjoint genes (compatibility_disjoint), a weight for homologous genes
+ * (compatibility_homologous) and a speciation threshold; the gene interface
+ * gives every gene a distance.  The paper states no formula, so this oracle
+ * fixes the following reading:
+ *   - genes are the present rows of N^ and C^ (inputs included; disabled
+ *     connections included).  Node genes are homologous when their keys are
+ *     equal, connection genes when their (in key, out key) pairs are equal;
+ *     a gene present in only one genome is disjoint (no excess/disjoint
+ *     distinction: the paper has one weight).
+ *   - node gene distance |bias diff| + |response diff| + [aggregation ids
+ *     differ] + [activation ids differ]; connection gene distance
+ *     |weight diff| + [enabled flags differ], enabled <=> e != 0.
+ *   - d = (c_d D_n + c_h S_n) / max(n_a, n_b) + (c_d D_c + c_h S_c) / max(m_a, m_b),
+ *     D = disjoint count, S = sum of homologous gene distances, n / m = the
+ *     genomes' node / connection gene counts; a term whose denominator is 0
+ *     is 0.
+ *   - a genome with a non-integer key, a duplicated node key or a duplicated
+ *     connection pair has no well-defined homology: its distances are NaN.
+ * The matching is the plain all-pairs comparison of the two genomes' rows.
+ */
+static uint32_t gene_status(const float *nodes, const float *conns, int Nmax, int Cmax)
+{
+    uint32_t st = 0;
+    for (int r = 0; r < Nmax; r++) {
+        const float k = nodes[(size_t)r * 5];
+        if (isnan(k)) continue;
+        if (!is_key(k)) { st |= ORC_BADKEY; continue; }
+        for (int q = 0; q < r; q++)
+            if (nodes[(size_t)q * 5] == k) st |= ORC_DUPKEY;
+    }
+    for (int c = 0; c < Cmax; c++) {
+        const float *cn = conns + (size_t)c * 4;
+        if (isnan(cn[0]) || isnan(cn[1]) || isnan(cn[2])) continue;
+        if (!is_key(cn[0]) || !is_key(cn[1])) { st |= ORC_BADKEY; continue; }
+        for (int q = 0; q < c; q++) {
+            const float *cq = conns + (size_t)q * 4;
+            if (isnan(cq[0]) || isnan(cq[1]) || isnan(cq[2])) continue;
+            if (cq[0] == cn[0] && cq[1] == cn[1]) st |= ORC_DUPCONN;
+        }
+    }
+    return st;
+}
+
+static double pair_distance(const float *na, const float *ca, const float *nb, const float *cb,
+                            int Nmax, int Cmax, double c_d, double c_h)
+{
+    int n_a = 0, n_b = 0, hom = 0;
+    double s = 0.0;
+    for (int r = 0; r < Nmax; r++) n_a += !isnan(na[(size_t)r * 5]);
+    for (int r = 0; r < Nmax; r++) n_b += !isnan(nb[(size_t)r * 5]);
+    for (int i = 0; i < Nmax; i++) {
+        const float *x = na + (size_t)i * 5;
+        if (isnan(x[0])) continue;
+        for (int j = 0; j < Nmax; j++) {
+            const float *y = nb + (size_t)j * 5;
+            if (isnan(y[0]) || y[0] != x[0]) continue;
+            hom++;
+            s += fabs((double)x[1] - (double)y[1]) + fabs((double)x[2] - (double)y[2]) +
+                 (x[3] != y[3] ? 1.0 : 0.0) + (x[4] != y[4] ? 1.0 : 0.0);
+        }
+    }
+    const int nmax = n_a > n_b ? n_a : n_b;
+    const double d_nodes = nmax ? (c_d * (double)(n_a + n_b - 2 * hom) + c_h * s) / (double)nmax : 0.0;
+
+    int m_a = 0, m_b = 0;
+    hom = 0;
+    s = 0.0;
+    for (int c = 0; c < Cmax; c++) {
+        const float *x = ca + (size_t)c * 4;
+        m_a += !(isnan(x[0]) || isnan(x[1]) || isnan(x[2]));
+    }
+    for (int c = 0; c < Cmax; c++) {
+        const float *y = cb + (size_t)c * 4;
+        m_b += !(isnan(y[0]) || isnan(y[1]) || isnan(y[2]));
+    }
+    for (int i = 0; i < Cmax; i++) {
+        const float *x = ca + (size_t)i * 4;
+        if (isnan(x[0]) || isnan(x[1]) || isnan(x[2])) continue;
+        for (int j = 0; j < Cmax; j++) {
+            const float *y = cb + (size_t)j * 4;
+            if (isnan(y[0]) || isnan(y[1]) || isnan(y[2])) continue;
+            if (y[0] != x[0] || y[1] != x[1]) continue;
+            hom++;
+            s += fabs((double)x[3] - (double)y[3]) + (((x[2] != 0.0f) != (y[2] != 0.0f)) ? 1.0 : 0.0);
+        }
+    }
+    const int mmax = m_a > m_b ? m_a : m_b;
+    const double d_conns = mmax ? (c_d * (double)(m_a + m_b - 2 * hom) + c_h * s) / (double)mmax : 0.0;
+    return d_nodes + d_conns;
+}
+
+int oracle_distance(const float *nodes_a, const float *conns_a, int PA, const float *nodes_b,
+                    const float *conns_b, int PB, int Nmax, int Cmax, double c_d, double c_h,
+                    double *out, uint32_t *status_a, uint32_t *status_b)
+{
+    for (int a = 0; a < PA; a++)
+        status_a[a] = gene_status(nodes_a + (size_t)a * Nmax * 5, conns_a + (size_t)a * Cmax * 4, Nmax, Cmax);
+    for (int b = 0; b < PB; b++)
+        status_b[b] = gene_status(nodes_b + (size_t)b * Nmax * 5, conns_b + (size_t)b * Cmax * 4, Nmax, Cmax);
+    for (int a = 0; a < PA; a++)
+        for (int b = 0; b < PB; b++)
+            out[(size_t)a * PB + b] =
+                (status_a[a] | status_b[b]) ? NAN
+                                            : pair_distance(nodes_a + (size_t)a * Nmax * 5,
+                                                            conns_a + (size_t)a * Cmax * 4,
+                                                            nodes_b + (size_t)b * Nmax * 5,
+                                                            conns_b + (size_t)b * Cmax * 4, Nmax, Cmax, c_d, c_h);
+    return 0;
+}
