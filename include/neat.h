@@ -257,7 +257,7 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
 
 /*
- * Device error word of the forward, plan, CPPN and recurrent kernels: bit 0 is set when a
+ * Device error word of the forward, plan, CPPN, recurrent and distance kernels: bit 0 is set when a
  * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
  * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).
@@ -303,6 +303,56 @@ NEAT_API int neat_forward_recurrent_ex(const void *transformed_dev, int32_t pop,
 /* Default launch shape of the recurrent forward (host only; queries the
  * current device once). */
 NEAT_API int neat_default_launch_recurrent(int32_t pop, neat_dims d, int32_t batch, neat_launch *out);
+
+/* ------------------------------------------------- genome distance
+ *
+ * Distances between genomes for speciation (Algorithm 1 divides the
+ * population into species by distances between networks; the
+ * hyperparameters compatibility_disjoint and compatibility_homologous weight
+ * disjoint and homologous genes, and compatibility_threshold bounds a
+ * species).  The paper gives no formula; this library's definition:
+ *   genes are the present rows of the node tensor and the connection tensor
+ *   (inputs and disabled connections included); node genes are homologous
+ *   when their keys are equal, connection genes when their (in key, out key)
+ *   pairs are equal; every other gene is disjoint.
+ *   d(a, b) = (c_d D_n + c_h S_n) / max(n_a, n_b) + (c_d D_c + c_h S_c) / max(m_a, m_b)
+ *   D = number of disjoint genes, n / m = number of node / connection genes,
+ *   S_n = sum over homologous node pairs of |bias diff| + |response diff|
+ *         + [aggregation ids differ] + [activation ids differ],
+ *   S_c = sum over homologous connection pairs of |weight diff|
+ *         + [enabled flags differ] (enabled <=> value != 0);
+ *   a term whose denominator is 0 is 0.  A genome with a non-integer key
+ *   (NEAT_G_BADKEY), a duplicated node key (NEAT_G_DUPKEY) or a duplicated
+ *   connection pair (NEAT_G_DUPCONN) has NaN distances.
+ * Computed in float; results are deterministic (a function of the two
+ * genomes). */
+
+/* Bytes of one genome's gene record (a multiple of 128); 0 for invalid dims. */
+NEAT_API size_t neat_gene_stride(neat_dims d);
+
+/* Gene records of `pop` genomes (nodes f32 [pop][max_nodes][5], conns f32
+ * [pop][max_conns][4], device, conns 16-byte aligned) into genes_dev
+ * (>= pop * neat_gene_stride(d) bytes, 16-byte aligned, caller-owned):
+ * node keys and (in, out) pairs sorted, with their attributes.  status_dev
+ * (optional, u32 [pop]) receives the bits above (0 = valid).
+ * Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_distance_prepare(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                                   void *genes_dev, size_t genes_bytes, uint32_t *status_dev, void *stream);
+
+/* out_dev[i * ld_out + j] = d(a_i, b_j) for i < pop_a, j < pop_b, from gene
+ * records of the same dims (ld_out >= pop_b; a and b may be the same buffer).
+ * Errors: NEAT_EINVAL (sizes, alignment, a record above 200 KB), NEAT_ECUDA. */
+NEAT_API int neat_distance(const void *genes_a, int32_t pop_a, const void *genes_b, int32_t pop_b, neat_dims d,
+                           float c_disjoint, float c_homologous, float *out_dev, int64_t ld_out, void *stream);
+
+/* Species assignment from a distance matrix f32 [pop][ld] (device), columns
+ * 0..n_reps-1 being the species representatives: species_dev[i] = the column
+ * j with the smallest distance among those with distance < threshold (the
+ * lowest such column on ties), or -1 when there is none (a NaN distance never
+ * qualifies).  Creating new species for the -1 genomes is left to the caller.
+ * Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_speciate(const float *distances_dev, int32_t pop, int32_t n_reps, int64_t ld, float threshold,
+                           int32_t *species_dev, void *stream);
 
 /* ---------------------------------------------------------- CPPN query
  *

@@ -172,10 +172,9 @@ extern "C" int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_di
     if (smem > 200u * 1024u) return invalid("neat_cppn_query: genome too large for one block (max_nodes <= 160)");
     const long blocks = (long)pop * a.chunks;
     if (blocks > 0x7fffffffL) return invalid("neat_cppn_query: too many queries");
-    if (smem > 48u * 1024u) {
-        cudaError_t e = cudaFuncSetAttribute(cppn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "neat_cppn_query: cudaFuncSetAttribute");
-    }
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(cppn_kernel), smem,
+                                "neat_cppn_query: shared memory per block");
+    if (rc) return rc;
     cppn_kernel<<<(unsigned)blocks, kCppnThreads, smem, as_stream(stream)>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_cppn_query: launch");

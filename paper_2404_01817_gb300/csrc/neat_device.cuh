@@ -25,6 +25,35 @@ __device__ __forceinline__ float activate(uint32_t act, float z)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// A node or connection key: an exact integer in [0, 2^24).
+__device__ __forceinline__ bool is_key(float k)
+{
+    return !isnan(k) && k >= 0.0f && k < 16777216.0f && floorf(k) == k;
+}
+
+// In-place ascending bitonic sort of n2 (a power of two) keys in shared
+// memory; every thread of the block must call it.
+template <typename T>
+__device__ void bitonic_sort(T *a, int n2)
+{
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const T x = a[i], y = a[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Read-only 16-byte global load.
 __device__ __forceinline__ uint4 ldg16(const uint4 *p) { return __ldg(p); }
 

@@ -1,0 +1,606 @@
+// Genome distance for speciation (Algorithm 1 divides the population by
+// distances between networks; the hyperparameters weight disjoint and
+// homologous genes and set a speciation threshold).  Genes are the present
+// rows of the node and connection tensors (Section 3.1); node genes are
+// homologous when their keys match, connection genes when their (in key,
+// out key) pairs match.  For genomes a and b
+//   d = (c_d D_n + c_h S_n) / max(n_a, n_b) + (c_d D_c + c_h S_c) / max(m_a, m_b)
+// with D the disjoint gene count, S the sum over homologous pairs of
+// |bias diff| + |response diff| + [aggregation differs] + [activation differs]
+// (nodes) or |weight diff| + [enabled differs] (connections), n and m the
+// node and connection gene counts, and a term with a zero denominator 0.
+//
+// GB300 mapping:
+//  * neat_distance_prepare: one block per genome sorts its node keys and its
+//    connection key pairs in shared memory (bitonic) and writes a compact
+//    gene record: header, sorted node keys, node attributes, sorted pair
+//    keys, connection attributes.  Duplicates show up as equal neighbours.
+//  * neat_distance: a block stages a tile of up to 16 b-records in shared
+//    memory with TMA bulk copies (one mbarrier, bounded wait) and builds an
+//    open-addressing hash table of each record's node keys and connection
+//    pairs next to it (records too large for tables are searched by binary
+//    search in their sorted keys instead).  Its warps stream a-genomes from
+//    global memory (L2-resident across blocks): lane l loads a's genes l,
+//    l+32, ... once each and looks every one up in all staged b-records
+//    (independent lookups in flight, per-representative sums in registers);
+//    the counts and sums are reduced across the warp along a fixed tree, so
+//    every result is a function of the two genomes alone, whichever lookup
+//    finds the homologous gene.
+//  * neat_speciate: one warp per genome scans its distance row for the
+//    nearest representative under the threshold.
+#include <algorithm>
+
+#include "neat_device.cuh"
+#include "neat_internal.h"
+
+namespace neat {
+namespace {
+
+constexpr int kPrepThreads = 256;
+constexpr int kDistThreads = 256;
+constexpr int kDistWarps = kDistThreads / 32;
+constexpr int kMaxTile = 16;
+constexpr uint32_t kGeneHeaderBytes = 16;
+
+// Gene record offsets for n node genes and m connection genes.
+struct GeneLayout {
+    uint32_t nkey, nattr, ckey, cattr, used;
+};
+
+__host__ __device__ inline GeneLayout gene_layout(uint32_t n, uint32_t m)
+{
+    GeneLayout L;
+    L.nkey = kGeneHeaderBytes;
+    L.nattr = L.nkey + align16(4u * n);
+    L.ckey = L.nattr + 16u * n;
+    L.cattr = L.ckey + 8u * m;
+    L.used = align16(L.cattr + 8u * m);
+    return L;
+}
+
+inline size_t gene_stride(const neat_dims &d)
+{
+    const size_t b = gene_layout((uint32_t)d.max_nodes, (uint32_t)d.max_conns).used;
+    return (b + 127) & ~(size_t)127;
+}
+
+struct PrepArgs {
+    const float *nodes;
+    const float *conns;
+    uint8_t *out;
+    uint32_t *status;
+    size_t stride;
+    int N, C, Np2, Cp2;
+};
+
+__global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long *nk = reinterpret_cast<unsigned long long *>(sm);   // key << 32 | row
+    unsigned long long *ck = nk + a.Np2;                                     // (in << 24 | out) << 13 | row
+    __shared__ unsigned int st;
+    __shared__ int n_nodes, n_conns;
+    const int g = blockIdx.x, tid = threadIdx.x;
+    const float *nd = a.nodes + (size_t)g * a.N * 5;
+    const float4 *cn = reinterpret_cast<const float4 *>(a.conns + (size_t)g * a.C * 4);
+    if (tid == 0) {
+        st = 0;
+        n_nodes = 0;
+        n_conns = 0;
+    }
+    __syncthreads();
+    unsigned int lst = 0;
+    for (int r = tid; r < a.Np2; r += kPrepThreads) {
+        unsigned long long v = ~0ull;
+        if (r < a.N) {
+            const float k = __ldg(nd + (size_t)r * 5);
+            if (!isnan(k)) {
+                if (is_key(k)) {
+                    v = ((unsigned long long)(uint32_t)k << 32) | (unsigned)r;
+                    atomicAdd(&n_nodes, 1);
+                } else {
+                    lst |= NEAT_G_BADKEY;
+                }
+            }
+        }
+        nk[r] = v;
+    }
+    for (int c = tid; c < a.Cp2; c += kPrepThreads) {
+        unsigned long long v = ~0ull;
+        if (c < a.C) {
+            const float4 row = __ldg(cn + c);
+            if (!(isnan(row.x) || isnan(row.y) || isnan(row.z))) {
+                if (is_key(row.x) && is_key(row.y)) {
+                    const unsigned long long pair = ((unsigned long long)(uint32_t)row.x << 24) | (uint32_t)row.y;
+                    v = (pair << 13) | (unsigned)c;
+                    atomicAdd(&n_conns, 1);
+                } else {
+                    lst |= NEAT_G_BADKEY;
+                }
+            }
+        }
+        ck[c] = v;
+    }
+    if (lst) atomicOr(&st, lst);
+    __syncthreads();
+    bitonic_sort(nk, a.Np2);
+    bitonic_sort(ck, a.Cp2);
+    const int n = n_nodes, m = n_conns;
+    lst = 0;
+    for (int i = tid + 1; i < n; i += kPrepThreads)
+        if ((nk[i] >> 32) == (nk[i - 1] >> 32)) lst |= NEAT_G_DUPKEY;
+    for (int i = tid + 1; i < m; i += kPrepThreads)
+        if ((ck[i] >> 13) == (ck[i - 1] >> 13)) lst |= NEAT_G_DUPCONN;
+    if (lst) atomicOr(&st, lst);
+    __syncthreads();
+    const uint32_t status = st;
+    uint8_t *rec = a.out + (size_t)g * a.stride;
+    if (status) {
+        if (tid == 0) {
+            *reinterpret_cast<uint4 *>(rec) = make_uint4(0u, 0u, status, kGeneHeaderBytes);
+            if (a.status) a.status[g] = status;
+        }
+        return;
+    }
+    const GeneLayout L = gene_layout((uint32_t)n, (uint32_t)m);
+    uint32_t *okey = reinterpret_cast<uint32_t *>(rec + L.nkey);
+    uint4 *oattr = reinterpret_cast<uint4 *>(rec + L.nattr);
+    for (int j = tid; j < n; j += kPrepThreads) {
+        const unsigned long long v = nk[j];
+        const float *row = nd + (size_t)(v & 0xffffffffu) * 5;
+        okey[j] = (uint32_t)(v >> 32);
+        oattr[j] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
+                              __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
+    }
+    for (int j = n + tid; j < (int)((L.nattr - L.nkey) / 4); j += kPrepThreads) okey[j] = 0xffffffffu;   // pad
+    unsigned long long *ockey = reinterpret_cast<unsigned long long *>(rec + L.ckey);
+    float2 *ocattr = reinterpret_cast<float2 *>(rec + L.cattr);
+    for (int j = tid; j < m; j += kPrepThreads) {
+        const unsigned long long v = ck[j];
+        const float4 row = __ldg(cn + (v & 0x1fffu));
+        ockey[j] = v >> 13;
+        ocattr[j] = make_float2(row.w, row.z != 0.0f ? 1.0f : 0.0f);
+    }
+    if (tid == 0) {
+        *reinterpret_cast<uint4 *>(rec) = make_uint4((uint32_t)n, (uint32_t)m, 0u, L.used);
+        if (a.status) a.status[g] = 0u;
+    }
+}
+
+struct DistArgs {
+    const uint8_t *a;
+    const uint8_t *b;
+    size_t stride;
+    int pa, pb;
+    float cd, ch;
+    float *out;
+    long long ldo;
+    int tile;             // b-records per block
+    int a_per_block;      // a-genomes per block
+    uint32_t slot_bytes;  // shared memory per staged b-record: the record, then (HASH) its two tables
+    uint32_t lgn, lgc;    // log2 of the node / connection hash-table capacities (HASH)
+};
+
+__device__ unsigned int g_distance_error;
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+// Index of `key` among n ascending keys, or -1.
+template <typename K>
+__device__ __forceinline__ int find_key(const K *keys, int n, K key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == key) ? lo : -1;
+}
+
+// Open addressing with linear probing.  Node table entries: key << 32 |
+// index; connection table entries: (in << 24 | out) << 13 | index; kEmpty
+// marks a free slot.  Capacities are powers of two above 1.5x the gene
+// count, so a probe sequence always reaches a free slot.
+__device__ __forceinline__ uint32_t slot_of(uint32_t x, uint32_t lg) { return (x * 0x9E3779B1u) >> (32u - lg); }
+
+__device__ __forceinline__ uint32_t fold_pair(unsigned long long pair)
+{
+    return (uint32_t)pair * 0x85EBCA6Bu ^ (uint32_t)(pair >> 32);
+}
+
+__device__ __forceinline__ void table_insert(unsigned long long *tab, uint32_t lg, uint32_t slot,
+                                             unsigned long long v)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        if (atomicCAS(tab + slot, kEmpty, v) == kEmpty) return;
+        slot = (slot + 1u) & mask;
+    }
+}
+
+__device__ __forceinline__ int node_lookup(const unsigned long long *tab, uint32_t lg, uint32_t key)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(key, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long v = tab[s];
+        if (v == kEmpty) return -1;
+        if ((uint32_t)(v >> 32) == key) return (int)(uint32_t)v;
+        s = (s + 1u) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int conn_lookup(const unsigned long long *tab, uint32_t lg, unsigned long long pair)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(fold_pair(pair), lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long v = tab[s];
+        if (v == kEmpty) return -1;
+        if ((v >> 13) == pair) return (int)(v & 0x1fffu);
+        s = (s + 1u) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <bool HASH>
+__global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ uint64_t bar_mem;
+    __shared__ int failed;
+    __shared__ uint32_t s_n[kMaxTile], s_m[kMaxTile], s_st[kMaxTile], s_nattr[kMaxTile], s_ckey[kMaxTile],
+        s_cattr[kMaxTile];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b0 = blockIdx.y * p.tile;
+    const int nb = min(p.tile, p.pb - b0);
+    const uint32_t bar = smem_addr(&bar_mem);
+    if (tid == 0) {
+        // copy sizes: the record's used bytes, never more than its stride
+        failed = 0;
+        uint32_t total = 0;
+        for (int t = 0; t < nb; ++t)
+            total += min(align16(__ldg(reinterpret_cast<const uint32_t *>(p.b + (size_t)(b0 + t) * p.stride) + 3)),
+                         (uint32_t)p.stride);
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, total);
+        for (int t = 0; t < nb; ++t) {
+            const uint8_t *src = p.b + (size_t)(b0 + t) * p.stride;
+            const uint32_t bytes = min(align16(__ldg(reinterpret_cast<const uint32_t *>(src) + 3)), (uint32_t)p.stride);
+            bulk_g2s(smem_addr(sm + (size_t)t * p.slot_bytes), src, bytes, bar);
+        }
+    }
+    if constexpr (HASH) {
+        // the tables sit after each record's stride, outside the copied bytes
+        const uint32_t words = (p.slot_bytes - (uint32_t)p.stride) / 8u;
+        for (int t = 0; t < nb; ++t) {
+            unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm + (size_t)t * p.slot_bytes + p.stride);
+            for (uint32_t i = tid; i < words; i += kDistThreads) tab[i] = kEmpty;
+        }
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0)) failed = 1;
+    __syncthreads();
+    const int a_begin = blockIdx.x * p.a_per_block;
+    const int a_end = min(p.pa, a_begin + p.a_per_block);
+    if (failed) {
+        if (tid == 0) atomicOr(&g_distance_error, kErrWaitExpired);
+        mbar_wait(bar, 0);
+        for (int a = a_begin + warp; a < a_end; a += kDistWarps)
+            for (int t = lane; t < nb; t += 32) p.out[(size_t)a * p.ldo + b0 + t] = __int_as_float(0x7fc00000);
+        return;
+    }
+    if (tid < nb) {
+        const uint4 hb = *reinterpret_cast<const uint4 *>(sm + (size_t)tid * p.slot_bytes);
+        const GeneLayout Lb = gene_layout(hb.x, hb.y);
+        s_n[tid] = hb.x;
+        s_m[tid] = hb.y;
+        s_st[tid] = hb.z;
+        s_nattr[tid] = Lb.nattr;
+        s_ckey[tid] = Lb.ckey;
+        s_cattr[tid] = Lb.cattr;
+    }
+    if constexpr (HASH) {
+        for (int t = 0; t < nb; ++t) {
+            unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+            const uint4 hb = *reinterpret_cast<const uint4 *>(rb);
+            const GeneLayout Lb = gene_layout(hb.x, hb.y);
+            unsigned long long *ntab = reinterpret_cast<unsigned long long *>(rb + p.stride);
+            unsigned long long *ctab = ntab + (1u << p.lgn);
+            const uint32_t *nkey = reinterpret_cast<const uint32_t *>(rb + Lb.nkey);
+            const unsigned long long *ckey = reinterpret_cast<const unsigned long long *>(rb + Lb.ckey);
+            for (uint32_t j = tid; j < hb.x; j += kDistThreads)
+                table_insert(ntab, p.lgn, slot_of(nkey[j], p.lgn), ((unsigned long long)nkey[j] << 32) | j);
+            for (uint32_t j = tid; j < hb.y; j += kDistThreads)
+                table_insert(ctab, p.lgc, slot_of(fold_pair(ckey[j]), p.lgc), (ckey[j] << 13) | j);
+        }
+    }
+    __syncthreads();
+    for (int a = a_begin + warp; a < a_end; a += kDistWarps) {
+        const uint8_t *ra = p.a + (size_t)a * p.stride;
+        const uint4 ha = __ldg(reinterpret_cast<const uint4 *>(ra));
+        const int n_a = (int)ha.x, m_a = (int)ha.y;
+        const GeneLayout La = gene_layout(ha.x, ha.y);
+        // lane t ends up with the totals of representative t
+        int my_hn = 0, my_hc = 0;
+        float my_sn = 0.0f, my_sc = 0.0f;
+        {
+            // node genes: each of a's genes is loaded once and looked up in
+            // every staged representative (independent lookups in flight)
+            int hn[kMaxTile];
+            float sn[kMaxTile];
+#pragma unroll
+            for (int t = 0; t < kMaxTile; ++t) {
+                hn[t] = 0;
+                sn[t] = 0.0f;
+            }
+            const uint32_t *ka = reinterpret_cast<const uint32_t *>(ra + La.nkey);
+            const uint4 *aa = reinterpret_cast<const uint4 *>(ra + La.nattr);
+            for (int j = lane; j < n_a; j += 32) {
+                const uint32_t key = __ldg(ka + j);
+                const uint4 x = __ldg(aa + j);
+#pragma unroll
+                for (int t = 0; t < kMaxTile; ++t) {
+                    if (t < nb) {
+                        const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+                        int i;
+                        if constexpr (HASH)
+                            i = node_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride), p.lgn, key);
+                        else
+                            i = find_key(reinterpret_cast<const uint32_t *>(rb + kGeneHeaderBytes), (int)s_n[t], key);
+                        if (i >= 0) {
+                            const uint4 y = reinterpret_cast<const uint4 *>(rb + s_nattr[t])[i];
+                            ++hn[t];
+                            sn[t] += fabsf(__uint_as_float(x.x) - __uint_as_float(y.x)) +
+                                     fabsf(__uint_as_float(x.y) - __uint_as_float(y.y)) +
+                                     ((__uint_as_float(x.z) != __uint_as_float(y.z)) ? 1.0f : 0.0f) +
+                                     ((__uint_as_float(x.w) != __uint_as_float(y.w)) ? 1.0f : 0.0f);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kMaxTile; ++t) {
+                if (t < nb) {
+                    const int h = __reduce_add_sync(0xffffffffu, hn[t]);
+                    const float v = warp_sum(sn[t]);
+                    if (lane == t) {
+                        my_hn = h;
+                        my_sn = v;
+                    }
+                }
+            }
+        }
+        {
+            // connection genes, the same way
+            int hc[kMaxTile];
+            float sc[kMaxTile];
+#pragma unroll
+            for (int t = 0; t < kMaxTile; ++t) {
+                hc[t] = 0;
+                sc[t] = 0.0f;
+            }
+            const unsigned long long *ka = reinterpret_cast<const unsigned long long *>(ra + La.ckey);
+            const float2 *aa = reinterpret_cast<const float2 *>(ra + La.cattr);
+            for (int j = lane; j < m_a; j += 32) {
+                const unsigned long long key = __ldg(ka + j);
+                const float2 x = __ldg(aa + j);
+#pragma unroll
+                for (int t = 0; t < kMaxTile; ++t) {
+                    if (t < nb) {
+                        const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+                        int i;
+                        if constexpr (HASH)
+                            i = conn_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride) + (1u << p.lgn),
+                                            p.lgc, key);
+                        else
+                            i = find_key(reinterpret_cast<const unsigned long long *>(rb + s_ckey[t]), (int)s_m[t], key);
+                        if (i >= 0) {
+                            const float2 y = reinterpret_cast<const float2 *>(rb + s_cattr[t])[i];
+                            ++hc[t];
+                            sc[t] += fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kMaxTile; ++t) {
+                if (t < nb) {
+                    const int h = __reduce_add_sync(0xffffffffu, hc[t]);
+                    const float v = warp_sum(sc[t]);
+                    if (lane == t) {
+                        my_hc = h;
+                        my_sc = v;
+                    }
+                }
+            }
+        }
+        if (lane < nb) {
+            float d;
+            if (ha.z | s_st[lane]) {
+                d = __int_as_float(0x7fc00000);
+            } else {
+                const int n_b = (int)s_n[lane], m_b = (int)s_m[lane];
+                const int nmax = max(n_a, n_b), mmax = max(m_a, m_b);
+                const float dn = nmax ? fmaf(p.cd, (float)(n_a + n_b - 2 * my_hn), p.ch * my_sn) / (float)nmax : 0.0f;
+                const float dc = mmax ? fmaf(p.cd, (float)(m_a + m_b - 2 * my_hc), p.ch * my_sc) / (float)mmax : 0.0f;
+                d = dn + dc;
+            }
+            p.out[(size_t)a * p.ldo + b0 + lane] = d;
+        }
+    }
+}
+
+// Nearest representative closer than the threshold (lowest index on ties),
+// -1 if none; NaN never qualifies.
+__global__ void __launch_bounds__(256) speciate_kernel(const float *dist, int pop, int reps, long long ld,
+                                                      float threshold, int32_t *species)
+{
+    const int g = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= pop) return;
+    float best = __int_as_float(0x7f800000);
+    int bi = -1;
+    for (int s = lane; s < reps; s += 32) {
+        const float d = __ldg(dist + (size_t)g * ld + s);
+        if (d < threshold && d < best) {
+            best = d;
+            bi = s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ob < best || (ob == best && oi < bi))) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    if (lane == 0) species[g] = bi;
+}
+
+int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+int read_distance_error(unsigned int *v, int clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_distance_error, sizeof(*v));
+    if (e != cudaSuccess) return cuda_fail(e, "distance error word: read");
+    if (clear) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_distance_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_fail(e, "distance error word: clear");
+    }
+    return NEAT_OK;
+}
+
+}  // namespace neat
+
+using namespace neat;
+
+extern "C" size_t neat_gene_stride(neat_dims d)
+{
+    return dims_ok(d) ? gene_stride(d) : 0;
+}
+
+extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                                     void *genes_dev, size_t genes_bytes, uint32_t *status_dev, void *stream)
+{
+    clear_error();
+    if (!dims_ok(d)) return invalid("neat_distance_prepare: invalid dims");
+    if (pop < 0) return invalid("neat_distance_prepare: pop < 0");
+    if (pop == 0) return NEAT_OK;
+    if (!nodes_dev || !conns_dev || !genes_dev) return invalid("neat_distance_prepare: null pointer");
+    if ((reinterpret_cast<uintptr_t>(conns_dev) & 15u) || (reinterpret_cast<uintptr_t>(genes_dev) & 15u))
+        return invalid("neat_distance_prepare: conns and genes must be 16-byte aligned");
+    PrepArgs a;
+    a.nodes = nodes_dev;
+    a.conns = conns_dev;
+    a.out = static_cast<uint8_t *>(genes_dev);
+    a.status = status_dev;
+    a.stride = gene_stride(d);
+    if (genes_bytes < a.stride * (size_t)pop) return invalid("neat_distance_prepare: genes buffer too small");
+    a.N = d.max_nodes;
+    a.C = d.max_conns;
+    a.Np2 = next_pow2(a.N);
+    a.Cp2 = next_pow2(a.C > 0 ? a.C : 1);
+    const size_t smem = 8u * ((size_t)a.Np2 + (size_t)a.Cp2);
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(prepare_kernel), smem,
+                                "neat_distance_prepare: shared memory per block");
+    if (rc) return rc;
+    prepare_kernel<<<pop, kPrepThreads, smem, as_stream(stream)>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_distance_prepare: launch");
+    return NEAT_OK;
+}
+
+extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *genes_b, int32_t pop_b, neat_dims d,
+                             float c_disjoint, float c_homologous, float *out_dev, int64_t ld_out, void *stream)
+{
+    clear_error();
+    if (!dims_ok(d)) return invalid("neat_distance: invalid dims");
+    if (pop_a < 0 || pop_b < 0) return invalid("neat_distance: populations must be >= 0");
+    if (pop_a == 0 || pop_b == 0) return NEAT_OK;
+    if (!genes_a || !genes_b || !out_dev) return invalid("neat_distance: null pointer");
+    if (ld_out < pop_b) return invalid("neat_distance: ld_out < pop_b");
+    if ((reinterpret_cast<uintptr_t>(genes_a) & 15u) || (reinterpret_cast<uintptr_t>(genes_b) & 15u))
+        return invalid("neat_distance: gene records must be 16-byte aligned");
+    DistArgs p;
+    p.a = static_cast<const uint8_t *>(genes_a);
+    p.b = static_cast<const uint8_t *>(genes_b);
+    p.stride = gene_stride(d);
+    p.pa = pop_a;
+    p.pb = pop_b;
+    p.cd = c_disjoint;
+    p.ch = c_homologous;
+    p.out = out_dev;
+    p.ldo = ld_out;
+    const size_t budget = 200u * 1024u, shared_budget = 76u * 1024u;   // one block / three blocks per SM
+    if (p.stride > budget) return invalid("neat_distance: gene record exceeds 200 KB of shared memory");
+    // hash tables of capacity 2^lg > 1.5x the largest gene count, when they fit
+    auto lg_cap = [](int n) {
+        uint32_t lg = 1;
+        while ((1u << lg) < (uint32_t)(n + n / 2 + 1)) ++lg;
+        return lg;
+    };
+    p.lgn = lg_cap(d.max_nodes);
+    p.lgc = lg_cap(d.max_conns);
+    const size_t slot_hash = p.stride + 8u * ((size_t(1) << p.lgn) + (size_t(1) << p.lgc));
+    const bool hash = slot_hash <= budget;
+    p.slot_bytes = (uint32_t)(hash ? slot_hash : p.stride);
+    const size_t per_block = p.slot_bytes <= shared_budget ? shared_budget : budget;
+    p.tile = (int)std::min<size_t>({(size_t)kMaxTile, per_block / p.slot_bytes, (size_t)pop_b});
+    const int tiles = (pop_b + p.tile - 1) / p.tile;
+    if (tiles > 65535) return invalid("neat_distance: too many b-genomes");
+    const size_t smem = (size_t)p.tile * p.slot_bytes;
+    int dev = 0, sms = 152, smem_sm = 228 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    // one wave: as many blocks as fit at once, the a-genomes split evenly
+    const int resident = std::max(1, std::min(3, (int)(smem_sm / (smem + 1024u))));
+    const long want_x = std::max<long>(1, ((long)sms * resident + tiles - 1) / tiles);
+    long apb = (pop_a + want_x - 1) / want_x;
+    apb = std::max<long>(kDistWarps, (apb + kDistWarps - 1) / kDistWarps * kDistWarps);
+    p.a_per_block = (int)std::min<long>(apb, 1L << 30);
+    const long gx = (pop_a + p.a_per_block - 1) / p.a_per_block;
+    auto kern = hash ? distance_kernel<true> : distance_kernel<false>;
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_distance: shared memory per block");
+    if (rc) return rc;
+    kern<<<dim3((unsigned)gx, (unsigned)tiles), kDistThreads, smem, as_stream(stream)>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_distance: launch");
+    return NEAT_OK;
+}
+
+extern "C" int neat_speciate(const float *distances_dev, int32_t pop, int32_t n_reps, int64_t ld, float threshold,
+                             int32_t *species_dev, void *stream)
+{
+    clear_error();
+    if (pop < 0 || n_reps < 0) return invalid("neat_speciate: sizes must be >= 0");
+    if (pop == 0) return NEAT_OK;
+    if (!species_dev || (n_reps > 0 && !distances_dev)) return invalid("neat_speciate: null pointer");
+    if (ld < n_reps) return invalid("neat_speciate: ld < n_reps");
+    const long threads = (long)pop * 32;
+    speciate_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, as_stream(stream)>>>(distances_dev, pop, n_reps, ld,
+                                                                                      threshold, species_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_speciate: launch");
+    return NEAT_OK;
+}

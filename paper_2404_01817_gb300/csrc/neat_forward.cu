@@ -184,19 +184,9 @@ KernelFn pick(bool pdl, bool t1)
 
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
-std::mutex g_attr_mu;
-std::unordered_map<const void *, size_t> g_attr_bytes;   // dynamic smem already allowed per kernel
-
 int ensure_smem(KernelFn f, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return NEAT_OK;
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    size_t &have = g_attr_bytes[reinterpret_cast<const void *>(f)];
-    if (have >= bytes) return NEAT_OK;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return cuda_fail(e, "forward: cudaFuncSetAttribute");
-    have = 227 * 1024;
-    return NEAT_OK;
+    return allow_dynamic_smem(reinterpret_cast<const void *>(f), bytes, "forward: shared memory per block");
 }
 
 }  // namespace
@@ -531,12 +521,13 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
         e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
         if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
     }
-    unsigned int vp = 0, vc = 0, vr = 0;
+    unsigned int vp = 0, vc = 0, vr = 0, vd = 0;
     int rc = read_plan_error(&vp, clear);
     if (rc == NEAT_OK) rc = read_cppn_error(&vc, clear);
     if (rc == NEAT_OK) rc = read_rnn_error(&vr, clear);
+    if (rc == NEAT_OK) rc = read_distance_error(&vd, clear);
     if (rc) return rc;
-    *out_host = v | vp | vc | vr;
+    *out_host = v | vp | vc | vr | vd;
     return NEAT_OK;
 }
 

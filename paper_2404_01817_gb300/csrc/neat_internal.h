@@ -44,6 +44,15 @@ inline size_t record_stride(const neat_dims &d)
 
 bool dims_ok(const neat_dims &d);
 
+// Shared memory per block on sm_103 (static + dynamic).
+constexpr size_t kMaxSmemPerBlock = 227u * 1024u;
+
+// Let `kernel` launch with `dynamic_bytes` of dynamic shared memory on the
+// current device, counting its static shared memory: raises the kernel's
+// limit when static + dynamic exceeds the 48 KB default (never lowers it).
+// NEAT_EINVAL (message `what`) when the total exceeds kMaxSmemPerBlock.
+int allow_dynamic_smem(const void *kernel, size_t dynamic_bytes, const char *what);
+
 // ---------------------------------------------------------- forward args
 struct ForwardArgs {
     const uint8_t *rec;      // records, one per genome, `stride` bytes apart
@@ -103,6 +112,7 @@ int launch_plan_table(const BucketDev *table_dev, int nb, int total_items, unsig
 int read_plan_error(unsigned int *v, int clear);   // neat_plan.cu
 int read_cppn_error(unsigned int *v, int clear);   // neat_cppn.cu
 int read_rnn_error(unsigned int *v, int clear);    // neat_recurrent.cu
+int read_distance_error(unsigned int *v, int clear);   // neat_distance.cu
 // Groups per block that put `items` groups of `group` threads, each needing
 // `per_group` bytes of shared memory, in the fewest waves with the busiest SM
 // least loaded (neat_forward.cu).

@@ -257,8 +257,8 @@ int layout(neat_plan *P, cudaStream_t s)
         if (e != cudaSuccess) return cuda_fail(e, "plan: cudaFuncGetAttributes");
         if (P->smem + fa.sharedSizeBytes > 227u * 1024u)
             return invalid("plan: shared memory per block exceeds 227 KB; use a smaller tile");
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
-        if (e != cudaSuccess) return cuda_fail(e, "plan: cudaFuncSetAttribute");
+        const int rc = allow_dynamic_smem(reinterpret_cast<const void *>(f), P->smem, "plan: shared memory per block");
+        if (rc) return rc;
     }
     if (P->exec) {
         cudaGraphExecDestroy(P->exec);
@@ -833,9 +833,10 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
     if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaFuncGetAttributes");
     if (smem + fa.sharedSizeBytes > 227u * 1024u)
         return invalid("neat_forward_multi_noalloc: shared memory per block exceeds 227 KB");
-    if (smem > 48u * 1024u) {
-        e = cudaFuncSetAttribute(plan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: cudaFuncSetAttribute");
+    {
+        const int rc = allow_dynamic_smem(reinterpret_cast<const void *>(plan_kernel<false>), smem,
+                                          "neat_forward_multi_noalloc: shared memory per block");
+        if (rc) return rc;
     }
     e = cudaMemsetAsync(base, 0, sizeof(unsigned int), s);               // the work counter starts at zero
     if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: counter reset");
@@ -906,9 +907,10 @@ int launch_plan_table(const BucketDev *table_dev, int nb, int total_items, unsig
     cudaError_t e = cudaFuncGetAttributes(&fa, plan_kernel<false>);
     if (e != cudaSuccess) return cuda_fail(e, "plan table: cudaFuncGetAttributes");
     if (smem + fa.sharedSizeBytes > 227u * 1024u) return invalid("plan table: shared memory exceeds 227 KB");
-    if (smem > 48u * 1024u) {
-        e = cudaFuncSetAttribute(plan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "plan table: cudaFuncSetAttribute");
+    {
+        const int rc = allow_dynamic_smem(reinterpret_cast<const void *>(plan_kernel<false>), smem,
+                                          "plan table: shared memory per block");
+        if (rc) return rc;
     }
     int dev = 0, sms = 152, smem_sm = 233472;
     cudaGetDevice(&dev);

@@ -221,10 +221,8 @@ extern "C" int neat_forward_recurrent_ex(const void *transformed_dev, int32_t po
     ra.f = f;
     ra.iterations = iterations;
     RnnFn kern = pick_rnn(L.pdl != 0, L.tile == 1);
-    if (smem > 48u * 1024u) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "neat_forward_recurrent: cudaFuncSetAttribute");
-    }
+    rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_forward_recurrent: shared memory per block");
+    if (rc) return rc;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)(L.group * L.groups_per_block));

@@ -31,37 +31,9 @@ struct TransformArgs {
     int recurrent;  // cycles allowed: no Kahn order, every present node in level 0 (row order)
 };
 
-__device__ __forceinline__ bool is_key(float k)
-{
-    return !isnan(k) && k >= 0.0f && k < 16777216.0f && floorf(k) == k;
-}
-
 __device__ __forceinline__ bool is_enum(float v, int n)
 {
     return !isnan(v) && floorf(v) == v && v >= 0.0f && v < (float)n;
-}
-
-// In-place ascending bitonic sort of n2 (a power of two) keys; every thread
-// of the block must call it.
-template <typename T>
-__device__ void bitonic_sort(T *a, int n2)
-{
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const T x = a[i], y = a[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        a[i] = y;
-                        a[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
 }
 
 // Lowest row holding `key` among the n sorted (key << 32 | row) pairs, or -1.
@@ -350,15 +322,9 @@ static int transform_impl(const float *nodes_dev, const float *conns_dev, int32_
     a.recurrent = recurrent;
     const size_t smem = transform_smem_bytes(a.N, a.C, a.I, a.O, a.Np2, a.Cp2);
     const int threads = (a.N <= 64 && a.C <= 512) ? 128 : (a.N <= 256 && a.C <= 2048 ? 256 : 512);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)transform_smem_bytes(NEAT_MAX_NODES, NEAT_MAX_CONNS, 0,
-                                                                       NEAT_MAX_NODES, NEAT_MAX_NODES,
-                                                                       NEAT_MAX_CONNS));
-        if (e != cudaSuccess) return cuda_fail(e, "neat_transform: cudaFuncSetAttribute");
-        attr_set = true;
-    }
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(transform_kernel), smem,
+                                "neat_transform: shared memory per block");
+    if (rc) return rc;
     transform_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_transform: launch");

@@ -102,6 +102,11 @@ _sig = {
     "neat_forward_recurrent": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _i32, _P, _P]),
     "neat_forward_recurrent_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_default_launch_recurrent": (ctypes.c_int, [_i32, Dims, _i32, ctypes.POINTER(Launch)]),
+    "neat_gene_stride": (ctypes.c_size_t, [Dims]),
+    "neat_distance_prepare": (ctypes.c_int, [_P, _P, _i32, Dims, _P, ctypes.c_size_t, _P, _P]),
+    "neat_distance": (ctypes.c_int, [_P, _i32, _P, _i32, Dims, ctypes.c_float, ctypes.c_float, _P, ctypes.c_int64,
+                                     _P]),
+    "neat_speciate": (ctypes.c_int, [_P, _i32, _i32, ctypes.c_int64, ctypes.c_float, _P, _P]),
     "neat_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
@@ -256,6 +261,54 @@ def neat_forward_recurrent(transformed, pop: int, d: Dims, inputs, iterations: i
                                           ctypes.byref(launch) if launch is not None else None, _stream(stream)),
            "neat_forward_recurrent")
     return outputs
+
+
+def neat_gene_stride(d: Dims) -> int:
+    return int(_lib.neat_gene_stride(d))
+
+
+def neat_distance_prepare(nodes, conns, d: Dims, genes=None, status=None, stream=None):
+    """Gene records (sorted keys + attributes) of a population for
+    neat_distance.  Returns (genes uint8 tensor, status int32 tensor [P])."""
+    import torch
+    pop = nodes.shape[0]
+    assert nodes.is_cuda and conns.is_cuda and nodes.is_contiguous() and conns.is_contiguous()
+    assert tuple(nodes.shape[1:]) == (d.max_nodes, 5) and tuple(conns.shape[1:]) == (d.max_conns, 4)
+    nbytes = neat_gene_stride(d) * pop
+    if genes is None:
+        genes = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=nodes.device)
+    if status is None:
+        status = torch.empty(max(pop, 1), dtype=torch.int32, device=nodes.device)
+    _check(_lib.neat_distance_prepare(_ptr(nodes), _ptr(conns), pop, d, _ptr(genes),
+                                      genes.numel() * genes.element_size(), _ptr(status), _stream(stream)),
+           "neat_distance_prepare")
+    return genes, status[:pop]
+
+
+def neat_distance(genes_a, pop_a: int, genes_b, pop_b: int, d: Dims, c_disjoint: float, c_homologous: float,
+                  out=None, stream=None):
+    """Distance matrix f32 [pop_a][pop_b] between two prepared populations."""
+    import torch
+    if out is None:
+        out = torch.empty((pop_a, pop_b), dtype=torch.float32, device=genes_a.device)
+    ld = out.stride(0) if out.dim() == 2 and pop_a > 0 else max(pop_b, 1)
+    assert out.dtype == torch.float32 and (out.dim() != 2 or out.stride(1) == 1)
+    _check(_lib.neat_distance(_ptr(genes_a), pop_a, _ptr(genes_b), pop_b, d, c_disjoint, c_homologous, _ptr(out),
+                              max(ld, pop_b), _stream(stream)), "neat_distance")
+    return out
+
+
+def neat_speciate(distances, threshold: float, n_reps: int | None = None, species=None, stream=None):
+    """Nearest representative under the threshold per row (int32 [pop], -1 = none)."""
+    import torch
+    pop = distances.shape[0]
+    reps = distances.shape[1] if n_reps is None else n_reps
+    assert distances.dtype == torch.float32 and distances.stride(1) == 1
+    if species is None:
+        species = torch.empty(max(pop, 1), dtype=torch.int32, device=distances.device)
+    _check(_lib.neat_speciate(_ptr(distances), pop, reps, distances.stride(0), threshold, _ptr(species),
+                              _stream(stream)), "neat_speciate")
+    return species[:pop]
 
 
 def neat_forward(transformed, pop: int, d: Dims, inputs, outputs=None, launch: Launch | None = None,

@@ -357,3 +357,71 @@ def ant_recurrent_population(seed: int = 0, pop: int = 10000) -> Population:
     return random_recurrent_population(seed, pop, 27, 8, 50, 200,
                                        hidden=lambda r: int(r.integers(0, 16)),
                                        edges=lambda r, n: int(r.integers(100, 201)), stream=21)
+
+
+def related_population(seed: int, pop: int, num_inputs: int, num_outputs: int, max_nodes: int, max_conns: int,
+                       ancestor_hidden: int, ancestor_edges: int, new_nodes: int, new_conns: int,
+                       key_pool: int, p_perturb: float = 0.8, sigma: float = 0.5, p_flip: float = 0.05,
+                       p_drop: float = 0.1, p_act: float = 0.05, stream: int = 30) -> Population:
+    """A population in mid-evolution, for genome distances: mutated copies of
+    one random ancestor DAG.  Each member perturbs weights and biases
+    (N(0, sigma), probability p_perturb), flips enabled flags (p_flip), drops
+    connections (p_drop), changes activations (p_act), and adds up to
+    `new_nodes` hidden nodes whose keys come from a shared pool of `key_pool`
+    keys (so added genes are often homologous across members) and up to
+    `new_conns` connections between present nodes.  Rows are shuffled."""
+    I, O = num_inputs, num_outputs
+    anc = random_dag_population(seed, 1, I, O, max_nodes, max_conns, hidden=lambda r: ancestor_hidden,
+                                edges=lambda r, n: ancestor_edges, acts=ALL_ACTS, aggs=ALL_AGGS,
+                                p_disabled=0.1, stream=stream)
+    an = anc.nodes[0][~np.isnan(anc.nodes[0, :, 0])]
+    ac = anc.conns[0][~np.isnan(anc.conns[0, :, 0])]
+    base_key = int(an[:, 0].max()) + 1
+    P = empty_population(pop, max_nodes, max_conns, I, O)
+    for g in range(pop):
+        rng = rng_for(seed, stream + 1, g)
+        nodes = an.copy()
+        pert = rng.random(len(nodes)) < p_perturb
+        nodes[pert, 1] += (sigma * rng.standard_normal(int(pert.sum()))).astype(np.float32)
+        newact = rng.random(len(nodes)) < p_act
+        nodes[newact, 4] = rng.integers(0, 7, size=int(newact.sum()))
+        conns = ac[rng.random(len(ac)) >= p_drop].copy()
+        pert = rng.random(len(conns)) < p_perturb
+        conns[pert, 3] += (sigma * rng.standard_normal(int(pert.sum()))).astype(np.float32)
+        flip = rng.random(len(conns)) < p_flip
+        conns[flip, 2] = 1.0 - conns[flip, 2]
+        k = int(min(rng.integers(0, new_nodes + 1), max_nodes - len(nodes), key_pool))
+        if k > 0:
+            keys = base_key + rng.choice(key_pool, size=k, replace=False)
+            extra = np.zeros((k, NODE_COLS), np.float32)
+            extra[:, 0] = keys
+            extra[:, 1] = rng.standard_normal(k)
+            extra[:, 2] = 1.0
+            extra[:, 3] = rng.integers(0, 4, size=k)
+            extra[:, 4] = rng.integers(0, 7, size=k)
+            nodes = np.concatenate([nodes, extra])
+        present = nodes[:, 0].astype(np.int64)
+        targets = present[present >= I]
+        have = {(int(a), int(b)) for a, b in conns[:, :2]}
+        add = []
+        want = int(min(rng.integers(0, new_conns + 1), max_conns - len(conns)))
+        for _ in range(4 * want):
+            if len(add) >= want:
+                break
+            pair = (int(rng.choice(present)), int(rng.choice(targets)))
+            if pair not in have:
+                have.add(pair)
+                add.append((pair[0], pair[1], 1.0, float(rng.standard_normal())))
+        if add:
+            conns = np.concatenate([conns, np.asarray(add, np.float32)])
+        P.nodes[g, rng.permutation(max_nodes)[:len(nodes)]] = nodes
+        P.conns[g, rng.permutation(max_conns)[:len(conns)]] = conns
+    return P
+
+
+def ant_related_population(seed: int = 0, pop: int = 10000) -> Population:
+    """Ant-shaped population in mid-evolution (27 in, 8 out, max 50 nodes /
+    200 conns): an ancestor with 8 hidden nodes and 120 connections, members
+    adding up to 7 nodes from a pool of 20 keys and up to 30 connections."""
+    return related_population(seed, pop, 27, 8, 50, 200, ancestor_hidden=8, ancestor_edges=120, new_nodes=7,
+                              new_conns=30, key_pool=20)

@@ -70,3 +70,17 @@ def test_cppn_full_genomes_and_other_substrate(neat):
     g, b, s, t = np.meshgrid(np.arange(12), np.arange(3), np.arange(25), np.arange(25), indexing="ij")
     q = np.stack([g.ravel(), b.ravel(), s.ravel(), t.ravel()], 1).astype(np.int32)
     _check(w, pop, q, 5, thr=0.05)
+
+
+def test_cppn_shared_memory_at_the_default_limit(neat):
+    """Nmax 41: the dynamic shared memory (about 45.6 KB) is under 48 KB but
+    with the kernel's static shared memory over it, so the launch needs the
+    raised limit."""
+    pop = W.random_dag_population(9, 40, 5, 1, 41, 120, hidden=lambda r: int(r.integers(0, 36)),
+                                  edges=lambda r, n: int(r.integers(n, 3 * n)),
+                                  acts=(W.ACT_SIN, W.ACT_GAUSS, W.ACT_TANH, W.ACT_IDENTITY), aggs=(W.AGG_SUM,))
+    w = _run(neat, pop)
+    rng = np.random.default_rng(3)
+    q = np.stack([rng.integers(0, 40, 4000), rng.integers(0, 2, 4000), rng.integers(0, 256, 4000),
+                  rng.integers(0, 256, 4000)], 1).astype(np.int32)
+    _check(w, pop, q[np.argsort(q[:, 0], kind="stable")], 16)

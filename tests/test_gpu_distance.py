@@ -1,0 +1,180 @@
+"""Genome distance and species assignment through the C ABI
+(neat_distance_prepare, neat_distance, neat_speciate) against the FP64
+oracle.
+
+Distances pass within |gpu - ref| <= 1e-5 max(1, |ref|), NaN where the
+oracle has NaN; status words and species indices must match exactly (the
+species rule is applied by the oracle to the GPU's own float32 distances and
+threshold, so both sides decide in the same precision).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_01817_gb300 import workloads as W
+from tests.genome_helpers import genome, stack
+from tests.parity import assert_outputs_close
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "distance_handworked.json")
+
+
+@pytest.fixture(scope="module")
+def neat():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_01817_gb300 import neat as N
+    return N
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _prepare(neat, nodes, conns, I=3, O=2):
+    d = neat.dims(I, O, nodes.shape[1], conns.shape[1])
+    genes, st = neat.neat_distance_prepare(_dev(nodes), _dev(conns), d)
+    return d, genes, st.cpu().numpy().astype(np.uint32)
+
+
+def _distance(neat, a, b, cd=1.0, ch=0.5, I=3, O=2):
+    d, ga, sa = _prepare(neat, a[0], a[1], I, O)
+    _, gb, sb = _prepare(neat, b[0], b[1], I, O)
+    out = neat.neat_distance(ga, a[0].shape[0], gb, b[0].shape[0], d, cd, ch).cpu().numpy()
+    return out, sa, sb
+
+
+def _related(seed, pop, nmax=24, cmax=60):
+    return W.related_population(seed, pop, 3, 2, nmax, cmax, ancestor_hidden=6, ancestor_edges=20, new_nodes=6,
+                                new_conns=12, key_pool=10)
+
+
+def test_handworked_example(neat):
+    g = json.load(open(GOLD))
+    a = genome(g["a"]["nodes"], g["a"]["conns"], 6, 6)
+    b = genome(g["b"]["nodes"], g["b"]["conns"], 6, 6)
+    out, sa, sb = _distance(neat, a, b, g["c_disjoint"], g["c_homologous"])
+    assert sa[0] == 0 and sb[0] == 0
+    assert out[0, 0] == np.float32(g["distance"])             # dyadic values: exact in float32 too
+
+
+def test_gene_records(neat):
+    p = _related(1, 40)
+    d, genes, st = _prepare(neat, p.nodes, p.conns)
+    assert (st == 0).all()
+    stride = neat.neat_gene_stride(d)
+    raw = genes.cpu().numpy()[: 40 * stride].reshape(40, stride)
+    for g in range(40):
+        hdr = raw[g, :16].view(np.uint32)
+        keys = np.sort(p.nodes[g, ~np.isnan(p.nodes[g, :, 0]), 0]).astype(np.uint32)
+        present = ~np.isnan(p.conns[g, :, 0])
+        pairs = np.sort(p.conns[g, present, 0].astype(np.uint64) << np.uint64(24) |
+                        p.conns[g, present, 1].astype(np.uint64))
+        n, m = int(hdr[0]), int(hdr[1])
+        assert (n, m, int(hdr[2])) == (len(keys), len(pairs), 0)
+        np.testing.assert_array_equal(raw[g, 16:16 + 4 * n].view(np.uint32), keys)
+        off = 16 + ((4 * n + 15) // 16) * 16 + 16 * n
+        np.testing.assert_array_equal(raw[g, off:off + 8 * m].view(np.uint64), pairs)
+
+
+@pytest.mark.parametrize("cd,ch", [(1.0, 0.5), (2.0, 3.0)])
+def test_distances_match_oracle(neat, cd, ch):
+    a = _related(2, 70)
+    b = _related(3, 37)                          # another ancestor: mostly disjoint genes
+    mixed = (np.concatenate([a.nodes[:20], b.nodes[:17]]), np.concatenate([a.conns[:20], b.conns[:17]]))
+    out, sa, sb = _distance(neat, (a.nodes, a.conns), mixed, cd, ch)
+    ref, ra, rb = oracle.distance(a.nodes, a.conns, *mixed, cd, ch)
+    np.testing.assert_array_equal(sa, ra)
+    np.testing.assert_array_equal(sb, rb)
+    assert_outputs_close(out, ref, what=f"distance cd={cd} ch={ch}")
+    assert out[:, 20:].mean() > out[:, :20].mean()          # the other lineage is farther away
+
+
+def test_random_dag_populations_and_wide_genomes(neat):
+    p = W.random_dag_population(4, 30, 3, 2, 40, 120, hidden=lambda r: int(r.integers(0, 30)),
+                                edges=lambda r, n: int(r.integers(0, 3 * n)), acts=W.ALL_ACTS, aggs=W.ALL_AGGS,
+                                p_disabled=0.3)
+    out, _, _ = _distance(neat, (p.nodes, p.conns), (p.nodes, p.conns))
+    ref, _, _ = oracle.distance(p.nodes, p.conns, p.nodes, p.conns, 1.0, 0.5)
+    assert_outputs_close(out, ref, what="random DAGs")
+    assert (np.diag(out) == 0).all()
+    assert_outputs_close(out, out.T, what="symmetry")
+    # the largest genomes (1024 nodes, 8192 connections): one record per block
+    w = W.related_population(5, 3, 3, 2, 1024, 8192, ancestor_hidden=600, ancestor_edges=6000, new_nodes=300,
+                             new_conns=1500, key_pool=400)
+    out, _, _ = _distance(neat, (w.nodes, w.conns), (w.nodes, w.conns))
+    ref, _, _ = oracle.distance(w.nodes, w.conns, w.nodes, w.conns, 1.0, 0.5)
+    assert_outputs_close(out, ref, what="1024 nodes / 8192 conns")
+
+
+def test_tiling_does_not_change_bits(neat):
+    """A column of the distance matrix has the same bits whichever tile of
+    representatives, and whichever block of a-genomes, computes it."""
+    p = _related(6, 300)
+    d, genes, _ = _prepare(neat, p.nodes, p.conns)
+    full = neat.neat_distance(genes, 300, genes, 40, d, 1.0, 0.5).cpu().numpy()
+    stride = neat.neat_gene_stride(d)
+    part = neat.neat_distance(genes[7 * stride:], 290, genes[5 * stride:], 9, d, 1.0, 0.5).cpu().numpy()
+    np.testing.assert_array_equal(part, full[7:297, 5:14])
+
+
+def test_invalid_and_empty_genomes(neat):
+    ok = genome([(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1)], [(0, 1, 1, 0.5), None], 3, 2)
+    dupkey = genome([(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1), (1, 0.3, 1, 0, 1)], [(0, 1, 1, 0.5), None], 3, 2)
+    dupconn = genome([(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1)], [(0, 1, 1, 0.5), (0, 1, 0, 0.1)], 3, 2)
+    badkey = genome([(0, 0, 1, 0, 0), (1.5, 0.2, 1, 0, 1)], [(0, 1, 1, 0.5), None], 3, 2)
+    empty = genome([None, None, None], [None, None], 3, 2)
+    nodes, conns = stack([ok, dupkey, dupconn, badkey, empty])
+    out, sa, _ = _distance(neat, (nodes, conns), (nodes, conns), 1.5, 0.5, I=1, O=1)
+    ref, ra, _ = oracle.distance(nodes, conns, nodes, conns, 1.5, 0.5)
+    np.testing.assert_array_equal(sa, ra)
+    assert_outputs_close(out, ref, what="invalid/empty")
+    assert out[4, 4] == 0.0 and out[0, 4] == 3.0
+
+
+def test_speciate_matches_oracle(neat):
+    import torch
+    p = _related(7, 500)
+    d, genes, _ = _prepare(neat, p.nodes, p.conns)
+    reps = 48
+    dist = neat.neat_distance(genes, 500, genes, reps, d, 1.0, 0.5)
+    dist[13, :] = float("nan")
+    dist[14, 3] = float("nan")
+    host = dist.cpu().numpy()
+    for thr in (0.0, float(np.median(host[:, :reps][np.isfinite(host)])), 3.0):
+        thr32 = float(np.float32(thr))
+        sp = neat.neat_speciate(dist, thr32).cpu().numpy()
+        np.testing.assert_array_equal(sp, oracle.speciate(host.astype(np.float64), thr32))
+    sp = neat.neat_speciate(dist, 3.0).cpu().numpy()
+    own = np.arange(reps)
+    own[13] = -1                                               # row 13 is all NaN
+    np.testing.assert_array_equal(sp[:reps], own)              # a representative is its own nearest
+    # ties resolve to the lowest column
+    t = torch.tensor([[0.5, 0.25, 0.25, 0.25] * 10], device="cuda")
+    assert neat.neat_speciate(t, 1.0).cpu().numpy()[0] == 1
+    # a strided view: only the first n_reps columns are representatives
+    wide = torch.full((500, 64), 0.0, device="cuda")
+    wide[:, :reps] = dist
+    sp2 = neat.neat_speciate(wide, 3.0, n_reps=reps).cpu().numpy()
+    np.testing.assert_array_equal(sp2, sp)
+
+
+def test_ant_population_against_representatives(neat):
+    """10000 Ant-shaped genomes in mid-evolution against 64 representatives
+    (the benchmarked launch); 60 sampled rows against the oracle."""
+    p = W.ant_related_population(0, 10000)
+    d = neat.dims(27, 8, 50, 200)
+    genes, st = neat.neat_distance_prepare(_dev(p.nodes), _dev(p.conns), d)
+    reps = np.arange(0, 10000, 157)[:64]
+    rg, _ = neat.neat_distance_prepare(_dev(p.nodes[reps]), _dev(p.conns[reps]), d)
+    out = neat.neat_distance(genes, 10000, rg, 64, d, 1.0, 0.5).cpu().numpy()
+    idx = np.arange(0, 10000, 167)
+    ref, _, _ = oracle.distance(p.nodes[idx], p.conns[idx], p.nodes[reps], p.conns[reps], 1.0, 0.5)
+    assert_outputs_close(out[idx], ref, what="ant distances")
+    assert (st.cpu().numpy() == 0).all() and np.isfinite(out).all()
+    np.testing.assert_array_equal(out[reps, np.arange(64)], 0.0)
