@@ -150,3 +150,79 @@ def speciate(distances, threshold: float) -> np.ndarray:
         if best is not None:
             out[g] = best
     return out
+
+
+class MutationConfig(ctypes.Structure):
+    """Operator hyperparameters (the appendix's list; see neat_oracle.c for
+    how each is used)."""
+    _fields_ = [(n, ctypes.c_float) for n in (
+        "node_add", "node_delete", "conn_add", "conn_delete",
+        "bias_init_mean", "bias_init_std", "bias_mutate_power", "bias_mutate_rate", "bias_replace_rate",
+        "response_init_mean", "response_init_std", "response_mutate_power", "response_mutate_rate",
+        "response_replace_rate",
+        "weight_init_mean", "weight_init_std", "weight_mutate_power", "weight_mutate_rate", "weight_replace_rate",
+        "activation_replace_rate", "aggregation_replace_rate", "enabled_mutate_rate")] + [
+        ("activation_default", ctypes.c_int), ("aggregation_default", ctypes.c_int),
+        ("n_activation_options", ctypes.c_int), ("n_aggregation_options", ctypes.c_int),
+        ("activation_options", ctypes.c_int * 8), ("aggregation_options", ctypes.c_int * 4),
+        ("feedforward", ctypes.c_int)]
+
+
+def mutation_config(**kw) -> MutationConfig:
+    """All rates 0 and defaults (tanh, sum, response 1) unless given;
+    activation_options / aggregation_options as lists."""
+    m = MutationConfig()
+    m.response_init_mean = 1.0
+    m.activation_default, m.aggregation_default = 1, 0
+    m.feedforward = 1
+    acts = kw.pop("activation_options", [1])
+    aggs = kw.pop("aggregation_options", [0])
+    m.n_activation_options, m.n_aggregation_options = len(acts), len(aggs)
+    for i, a in enumerate(acts):
+        m.activation_options[i] = a
+    for i, a in enumerate(aggs):
+        m.aggregation_options[i] = a
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return m
+
+
+def mutation_words(max_nodes: int, max_conns: int) -> tuple[int, int]:
+    """(uint32 words, float normals) per genome."""
+    return 16 + 6 * max_nodes + 2 * max_conns, 4 + 2 * max_nodes + max_conns
+
+
+def mutate(nodes, conns, num_inputs: int, num_outputs: int, cfg: MutationConfig, words, normals, new_keys):
+    """Mutated copies (double) of P genomes; words uint32 [P][W], normals
+    f32 [P][Z], new_keys int32 [P]."""
+    nodes, conns = _genome_arrays(nodes, conns)
+    P, N, C = nodes.shape[0], nodes.shape[1], conns.shape[1]
+    W, Z = mutation_words(N, C)
+    words = np.ascontiguousarray(words, dtype=np.uint32).reshape(P, W)
+    normals = np.ascontiguousarray(normals, dtype=np.float32).reshape(P, Z)
+    new_keys = np.ascontiguousarray(new_keys, dtype=np.int32).reshape(P)
+    no = np.empty((P, N, 5), np.float64)
+    co = np.empty((P, C, 4), np.float64)
+    L = lib()
+    L.oracle_mutate.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int] * 5 + [ctypes.POINTER(MutationConfig)] + \
+        [ctypes.c_void_p] * 5
+    L.oracle_mutate(_ptr(nodes), _ptr(conns), P, num_inputs, num_outputs, N, C, ctypes.byref(cfg), _ptr(words),
+                    _ptr(normals), _ptr(new_keys), _ptr(no), _ptr(co))
+    return no, co
+
+
+def crossover(nodes, conns, parents, words):
+    """Children (float32) of parent pairs int32 [K][2] (first = fitter);
+    words uint32 [K][Nmax + Cmax]."""
+    nodes, conns = _genome_arrays(nodes, conns)
+    N, C = nodes.shape[1], conns.shape[1]
+    parents = np.ascontiguousarray(parents, dtype=np.int32).reshape(-1, 2)
+    K = parents.shape[0]
+    words = np.ascontiguousarray(words, dtype=np.uint32).reshape(K, N + C)
+    no = np.empty((K, N, 5), np.float32)
+    co = np.empty((K, C, 4), np.float32)
+    L = lib()
+    L.oracle_crossover.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 + [ctypes.c_void_p, ctypes.c_int] + \
+        [ctypes.c_void_p] * 3
+    L.oracle_crossover(_ptr(nodes), _ptr(conns), N, C, _ptr(parents), K, _ptr(words), _ptr(no), _ptr(co))
+    return no, co

@@ -679,3 +679,275 @@ int oracle_distance(const float *nodes_a, const float *conns_a, int PA, const fl
                                                             conns_b + (size_t)b * Cmax * 4, Nmax, Cmax, c_d, c_h);
     return 0;
 }
+
+/*
+ * Tensorized mutation and crossover (Section 3.2: node addition writes the
+ * first NaN row, removal writes NaN over a row, attribute modification
+ * overwrites one column; the operators are built from these).  The paper
+ * names the operator hyperparameters but not an algorithm; this oracle fixes
+ * the following reading.  Every random number is an input:
+ *   u[W] uint32 words per genome, W = 16 + 6 Nmax + 2 Cmax:
+ *     0..8 structural (below); node row r: 16 + 6r + {0 bias, 1 response,
+ *     2 activation decision, 3 activation choice, 4 aggregation decision,
+ *     5 aggregation choice}; connection row c: 16 + 6 Nmax + 2c + {0 weight,
+ *     1 enabled};
+ *   z[Z] float normals per genome, Z = 4 + 2 Nmax + Cmax: 0 new connection
+ *     weight; node row r: 4 + 2r + {0 bias, 1 response}; connection row c:
+ *     4 + 2 Nmax + c.
+ *   Bernoulli(p) with word u: u < T(p), T(p) = min(floor(p 2^32), 2^32)
+ *   (computed in double); choice among k with word u: floor(u k / 2^32).
+ * Present rows: node key not NaN; connection in, out and enabled not NaN.
+ * Free rows are the others; "first" means lowest row index.
+ * Structural steps, in order (each independent draw):
+ *   1. node addition (word 0): among present enabled connections pick one
+ *      (word 1); needs a free node row, two free connection rows and a new
+ *      key not present.  The connection is disabled; the first free node row
+ *      gets (new key, bias_init_mean, response_init_mean, aggregation
+ *      default, activation default); the first free connection row gets
+ *      (in, new, 1, 1.0) and the next (new, out, 1, old weight).
+ *   2. node deletion (word 2): among present nodes with key >= I + O pick
+ *      one (word 3); its row and every present connection row touching its
+ *      key become NaN.
+ *   3. connection addition (word 4): source among present nodes (word 5),
+ *      target among present nodes with key >= I (word 6).  An existing
+ *      present (source, target) row is enabled instead (the first such row);
+ *      otherwise, for feedforward networks, a self-loop or a target from
+ *      which the source is reachable through present connections is
+ *      rejected; otherwise the first free connection row gets (source,
+ *      target, 1, weight_init_mean + weight_init_std z[0]).
+ *   4. connection deletion (word 7): among present connections pick one
+ *      (word 8); its row becomes NaN.
+ * Attribute step, every present row afterwards: node rows with key >= I:
+ *   bias: u < T(mutate_rate) -> bias + mutate_power z;
+ *         else u < T(mutate_rate + replace_rate) -> init_mean + init_std z;
+ *   response the same with its own parameters;
+ *   activation: decision < T(replace_rate) -> options[choice];
+ *   aggregation the same.  Connection rows: weight as bias; enabled flips
+ *   (0 <-> 1, any non-zero counting as enabled) when its word < T(rate).
+ * Crossover of parents (p1, p2), p1 the fitter: the child is p1's tensors;
+ * a present row of p1 whose node key (connection (in, out) pair) is present
+ * in p2 takes p2's attributes (node: bias, response, aggregation,
+ * activation; connection: enabled, weight; p2's lowest such row) when its
+ * word u[row] (u[Nmax + row] for connections) is >= 2^31.
+ */
+typedef struct {
+    float node_add, node_delete, conn_add, conn_delete;
+    float bias_init_mean, bias_init_std, bias_mutate_power, bias_mutate_rate, bias_replace_rate;
+    float response_init_mean, response_init_std, response_mutate_power, response_mutate_rate, response_replace_rate;
+    float weight_init_mean, weight_init_std, weight_mutate_power, weight_mutate_rate, weight_replace_rate;
+    float activation_replace_rate, aggregation_replace_rate, enabled_mutate_rate;
+    int activation_default, aggregation_default;
+    int n_activation_options, n_aggregation_options;
+    int activation_options[8], aggregation_options[4];
+    int feedforward;
+} orc_mutation_t;
+
+static uint64_t thr_of(double p)
+{
+    if (!(p > 0.0)) return 0;
+    const double t = floor(p * 4294967296.0);
+    return t >= 4294967296.0 ? 4294967296ull : (uint64_t)t;
+}
+static int bern(uint32_t u, double p) { return (uint64_t)u < thr_of(p); }
+static int choice(uint32_t u, int k) { return (int)(((uint64_t)u * (uint64_t)k) >> 32); }
+
+static int node_present(const double *nd, int r) { return !isnan(nd[(size_t)r * 5]); }
+static int conn_present(const double *cn, int c)
+{
+    const double *x = cn + (size_t)c * 4;
+    return !(isnan(x[0]) || isnan(x[1]) || isnan(x[2]));
+}
+static int first_free_node(const double *nd, int N)
+{
+    for (int r = 0; r < N; r++) if (!node_present(nd, r)) return r;
+    return -1;
+}
+static int nth_free_conn(const double *cn, int C, int n)
+{
+    for (int c = 0; c < C; c++) if (!conn_present(cn, c) && n-- == 0) return c;
+    return -1;
+}
+
+/* is `to` reachable from `from` along present connections (keys)? */
+static int reachable(const double *nd, const double *cn, int N, int C, double from, double to)
+{
+    double *seen = malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    int ns = 0, found = (from == to);
+    seen[ns++] = from;
+    for (int changed = 1; changed && !found;) {
+        changed = 0;
+        for (int c = 0; c < C && !found; c++) {
+            if (!conn_present(cn, c)) continue;
+            const double a = cn[(size_t)c * 4], b = cn[(size_t)c * 4 + 1];
+            int has_a = 0, has_b = 0;
+            for (int i = 0; i < ns; i++) { has_a |= seen[i] == a; has_b |= seen[i] == b; }
+            if (has_a && !has_b) {
+                if (ns < N) seen[ns++] = b;
+                changed = 1;
+                if (b == to) found = 1;
+            }
+        }
+    }
+    (void)nd;
+    free(seen);
+    return found;
+}
+
+static void mutate_one(double *nd, double *cn, int I, int O, int N, int C, const orc_mutation_t *m,
+                       const uint32_t *u, const float *z, int new_key)
+{
+    /* 1. node addition */
+    if (bern(u[0], m->node_add)) {
+        int k = 0;
+        for (int c = 0; c < C; c++) k += conn_present(cn, c) && cn[(size_t)c * 4 + 2] != 0.0;
+        int key_used = 0;
+        for (int r = 0; r < N; r++) key_used |= node_present(nd, r) && nd[(size_t)r * 5] == (double)new_key;
+        const int rn = first_free_node(nd, N), ra = nth_free_conn(cn, C, 0), rb = nth_free_conn(cn, C, 1);
+        if (k > 0 && rn >= 0 && ra >= 0 && rb >= 0 && !key_used) {
+            int pick = choice(u[1], k), cs = -1;
+            for (int c = 0; c < C; c++)
+                if (conn_present(cn, c) && cn[(size_t)c * 4 + 2] != 0.0 && pick-- == 0) { cs = c; break; }
+            double *x = cn + (size_t)cs * 4;
+            const double in = x[0], out = x[1], w = x[3];
+            x[2] = 0.0;
+            double *n = nd + (size_t)rn * 5;
+            n[0] = new_key; n[1] = m->bias_init_mean; n[2] = m->response_init_mean;
+            n[3] = m->aggregation_default; n[4] = m->activation_default;
+            double *a = cn + (size_t)ra * 4, *b = cn + (size_t)rb * 4;
+            a[0] = in; a[1] = new_key; a[2] = 1.0; a[3] = 1.0;
+            b[0] = new_key; b[1] = out; b[2] = 1.0; b[3] = w;
+        }
+    }
+    /* 2. node deletion */
+    if (bern(u[2], m->node_delete)) {
+        int k = 0;
+        for (int r = 0; r < N; r++) k += node_present(nd, r) && nd[(size_t)r * 5] >= (double)(I + O);
+        if (k > 0) {
+            int pick = choice(u[3], k);
+            for (int r = 0; r < N; r++) {
+                if (!(node_present(nd, r) && nd[(size_t)r * 5] >= (double)(I + O)) || pick-- != 0) continue;
+                const double q = nd[(size_t)r * 5];
+                for (int j = 0; j < 5; j++) nd[(size_t)r * 5 + j] = NAN;
+                for (int c = 0; c < C; c++)
+                    if (conn_present(cn, c) && (cn[(size_t)c * 4] == q || cn[(size_t)c * 4 + 1] == q))
+                        for (int j = 0; j < 4; j++) cn[(size_t)c * 4 + j] = NAN;
+                break;
+            }
+        }
+    }
+    /* 3. connection addition */
+    if (bern(u[4], m->conn_add)) {
+        int ks = 0, kt = 0;
+        for (int r = 0; r < N; r++) {
+            ks += node_present(nd, r);
+            kt += node_present(nd, r) && nd[(size_t)r * 5] >= (double)I;
+        }
+        if (ks > 0 && kt > 0) {
+            int ps = choice(u[5], ks), pt = choice(u[6], kt);
+            double s = 0, t = 0;
+            for (int r = 0; r < N; r++) if (node_present(nd, r) && ps-- == 0) { s = nd[(size_t)r * 5]; break; }
+            for (int r = 0; r < N; r++)
+                if (node_present(nd, r) && nd[(size_t)r * 5] >= (double)I && pt-- == 0) { t = nd[(size_t)r * 5]; break; }
+            int existing = -1;
+            for (int c = 0; c < C; c++)
+                if (conn_present(cn, c) && cn[(size_t)c * 4] == s && cn[(size_t)c * 4 + 1] == t) { existing = c; break; }
+            if (existing >= 0) {
+                cn[(size_t)existing * 4 + 2] = 1.0;
+            } else if (!(m->feedforward && reachable(nd, cn, N, C, t, s))) {
+                const int rf = nth_free_conn(cn, C, 0);
+                if (rf >= 0) {
+                    double *x = cn + (size_t)rf * 4;
+                    x[0] = s; x[1] = t; x[2] = 1.0;
+                    x[3] = (double)m->weight_init_mean + (double)m->weight_init_std * (double)z[0];
+                }
+            }
+        }
+    }
+    /* 4. connection deletion */
+    if (bern(u[7], m->conn_delete)) {
+        int k = 0;
+        for (int c = 0; c < C; c++) k += conn_present(cn, c);
+        if (k > 0) {
+            int pick = choice(u[8], k);
+            for (int c = 0; c < C; c++)
+                if (conn_present(cn, c) && pick-- == 0) {
+                    for (int j = 0; j < 4; j++) cn[(size_t)c * 4 + j] = NAN;
+                    break;
+                }
+        }
+    }
+    /* attributes */
+    for (int r = 0; r < N; r++) {
+        if (!node_present(nd, r) || nd[(size_t)r * 5] < (double)I) continue;
+        double *n = nd + (size_t)r * 5;
+        const uint32_t *w = u + 16 + 6 * (size_t)r;
+        const float *zz = z + 4 + 2 * (size_t)r;
+        if (bern(w[0], m->bias_mutate_rate)) n[1] += (double)m->bias_mutate_power * (double)zz[0];
+        else if (bern(w[0], (double)m->bias_mutate_rate + (double)m->bias_replace_rate))
+            n[1] = (double)m->bias_init_mean + (double)m->bias_init_std * (double)zz[0];
+        if (bern(w[1], m->response_mutate_rate)) n[2] += (double)m->response_mutate_power * (double)zz[1];
+        else if (bern(w[1], (double)m->response_mutate_rate + (double)m->response_replace_rate))
+            n[2] = (double)m->response_init_mean + (double)m->response_init_std * (double)zz[1];
+        if (m->n_activation_options > 0 && bern(w[2], m->activation_replace_rate))
+            n[4] = m->activation_options[choice(w[3], m->n_activation_options)];
+        if (m->n_aggregation_options > 0 && bern(w[4], m->aggregation_replace_rate))
+            n[3] = m->aggregation_options[choice(w[5], m->n_aggregation_options)];
+    }
+    for (int c = 0; c < C; c++) {
+        if (!conn_present(cn, c)) continue;
+        double *x = cn + (size_t)c * 4;
+        const uint32_t *w = u + 16 + 6 * (size_t)N + 2 * (size_t)c;
+        const double zz = z[4 + 2 * (size_t)N + c];
+        if (bern(w[0], m->weight_mutate_rate)) x[3] += (double)m->weight_mutate_power * zz;
+        else if (bern(w[0], (double)m->weight_mutate_rate + (double)m->weight_replace_rate))
+            x[3] = (double)m->weight_init_mean + (double)m->weight_init_std * zz;
+        if (bern(w[1], m->enabled_mutate_rate)) x[2] = (x[2] != 0.0) ? 0.0 : 1.0;
+    }
+}
+
+int oracle_mutate(const float *nodes, const float *conns, int P, int I, int O, int N, int C,
+                  const orc_mutation_t *m, const uint32_t *u, const float *z, const int *new_keys,
+                  double *nodes_out, double *conns_out)
+{
+    const size_t W = 16 + 6 * (size_t)N + 2 * (size_t)C, Z = 4 + 2 * (size_t)N + (size_t)C;
+    for (int g = 0; g < P; g++) {
+        double *nd = nodes_out + (size_t)g * N * 5, *cn = conns_out + (size_t)g * C * 4;
+        for (size_t i = 0; i < (size_t)N * 5; i++) nd[i] = nodes[(size_t)g * N * 5 + i];
+        for (size_t i = 0; i < (size_t)C * 4; i++) cn[i] = conns[(size_t)g * C * 4 + i];
+        mutate_one(nd, cn, I, O, N, C, m, u + g * W, z + g * Z, new_keys[g]);
+    }
+    return 0;
+}
+
+int oracle_crossover(const float *nodes, const float *conns, int N, int C, const int *parents, int K,
+                     const uint32_t *u, float *nodes_out, float *conns_out)
+{
+    for (int k = 0; k < K; k++) {
+        const float *n1 = nodes + (size_t)parents[2 * k] * N * 5, *n2 = nodes + (size_t)parents[2 * k + 1] * N * 5;
+        const float *c1 = conns + (size_t)parents[2 * k] * C * 4, *c2 = conns + (size_t)parents[2 * k + 1] * C * 4;
+        float *no = nodes_out + (size_t)k * N * 5, *co = conns_out + (size_t)k * C * 4;
+        const uint32_t *w = u + (size_t)k * (N + C);
+        memcpy(no, n1, sizeof(float) * (size_t)N * 5);
+        memcpy(co, c1, sizeof(float) * (size_t)C * 4);
+        for (int r = 0; r < N; r++) {
+            if (isnan(n1[(size_t)r * 5]) || w[r] < 0x80000000u) continue;
+            for (int q = 0; q < N; q++) {
+                if (isnan(n2[(size_t)q * 5]) || n2[(size_t)q * 5] != n1[(size_t)r * 5]) continue;
+                memcpy(no + (size_t)r * 5 + 1, n2 + (size_t)q * 5 + 1, sizeof(float) * 4);
+                break;
+            }
+        }
+        for (int c = 0; c < C; c++) {
+            const float *x = c1 + (size_t)c * 4;
+            if (isnan(x[0]) || isnan(x[1]) || isnan(x[2]) || w[N + c] < 0x80000000u) continue;
+            for (int q = 0; q < C; q++) {
+                const float *y = c2 + (size_t)q * 4;
+                if (isnan(y[0]) || isnan(y[1]) || isnan(y[2]) || y[0] != x[0] || y[1] != x[1]) continue;
+                co[(size_t)c * 4 + 2] = y[2];
+                co[(size_t)c * 4 + 3] = y[3];
+                break;
+            }
+        }
+    }
+    return 0;
+}
