@@ -712,8 +712,8 @@ int oracle_distance(const float *nodes_a, const float *conns_a, int PA, const fl
  *      target among present nodes with key >= I (word 6).  An existing
  *      present (source, target) row is enabled instead (the first such row);
  *      otherwise, for feedforward networks, a self-loop or a target from
- *      which the source is reachable through present connections is
- *      rejected; otherwise the first free connection row gets (source,
+ *      which the source is reachable through present connections between
+ *      present nodes is rejected; otherwise the first free connection row gets (source,
  *      target, 1, weight_init_mean + weight_init_std z[0]).
  *   4. connection deletion (word 7): among present connections pick one
  *      (word 8); its row becomes NaN.
@@ -725,8 +725,8 @@ int oracle_distance(const float *nodes_a, const float *conns_a, int PA, const fl
  *   aggregation the same.  Connection rows: weight as bias; enabled flips
  *   (0 <-> 1, any non-zero counting as enabled) when its word < T(rate).
  * Crossover of parents (p1, p2), p1 the fitter: the child is p1's tensors;
- * a present row of p1 whose node key (connection (in, out) pair) is present
- * in p2 takes p2's attributes (node: bias, response, aggregation,
+ * a present row of p1 whose node key (connection (in, out) pair), a valid
+ * key, is present in p2 takes p2's attributes (node: bias, response, aggregation,
  * activation; connection: enabled, weight; p2's lowest such row) when its
  * word u[row] (u[Nmax + row] for connections) is >= 2^31.
  */
@@ -768,7 +768,14 @@ static int nth_free_conn(const double *cn, int C, int n)
     return -1;
 }
 
-/* is `to` reachable from `from` along present connections (keys)? */
+static int key_present(const double *nd, int N, double k)
+{
+    for (int r = 0; r < N; r++) if (node_present(nd, r) && nd[(size_t)r * 5] == k) return 1;
+    return 0;
+}
+
+/* is `to` reachable from `from` along present connections between present
+ * nodes (dangling connections take no part, as in the transform)? */
 static int reachable(const double *nd, const double *cn, int N, int C, double from, double to)
 {
     double *seen = malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
@@ -779,6 +786,7 @@ static int reachable(const double *nd, const double *cn, int N, int C, double fr
         for (int c = 0; c < C && !found; c++) {
             if (!conn_present(cn, c)) continue;
             const double a = cn[(size_t)c * 4], b = cn[(size_t)c * 4 + 1];
+            if (!key_present(nd, N, a) || !key_present(nd, N, b)) continue;
             int has_a = 0, has_b = 0;
             for (int i = 0; i < ns; i++) { has_a |= seen[i] == a; has_b |= seen[i] == b; }
             if (has_a && !has_b) {
@@ -930,7 +938,7 @@ int oracle_crossover(const float *nodes, const float *conns, int N, int C, const
         memcpy(no, n1, sizeof(float) * (size_t)N * 5);
         memcpy(co, c1, sizeof(float) * (size_t)C * 4);
         for (int r = 0; r < N; r++) {
-            if (isnan(n1[(size_t)r * 5]) || w[r] < 0x80000000u) continue;
+            if (!is_key(n1[(size_t)r * 5]) || w[r] < 0x80000000u) continue;
             for (int q = 0; q < N; q++) {
                 if (isnan(n2[(size_t)q * 5]) || n2[(size_t)q * 5] != n1[(size_t)r * 5]) continue;
                 memcpy(no + (size_t)r * 5 + 1, n2 + (size_t)q * 5 + 1, sizeof(float) * 4);
@@ -939,7 +947,7 @@ int oracle_crossover(const float *nodes, const float *conns, int N, int C, const
         }
         for (int c = 0; c < C; c++) {
             const float *x = c1 + (size_t)c * 4;
-            if (isnan(x[0]) || isnan(x[1]) || isnan(x[2]) || w[N + c] < 0x80000000u) continue;
+            if (!is_key(x[0]) || !is_key(x[1]) || isnan(x[2]) || w[N + c] < 0x80000000u) continue;
             for (int q = 0; q < C; q++) {
                 const float *y = c2 + (size_t)q * 4;
                 if (isnan(y[0]) || isnan(y[1]) || isnan(y[2]) || y[0] != x[0] || y[1] != x[1]) continue;

@@ -220,3 +220,17 @@ def test_crossover_rules():
     _same(co[1], np.array([(0, 1, 0, 0.9), (0, 4, 1, -0.6), (NAN,) * 4], np.float32))
     _same(no[2], a[0][0])                                  # a genome crossed with itself
     _same(co[2], a[1][0])
+
+
+def test_dangling_connections_do_not_make_paths():
+    # 2 -> 9 -> 3 with key 9 absent: adding 3 -> 2 closes no cycle among present nodes
+    rows = [(0, 0, 1, 0, 0), (1, 0, 1, 0, 1), (2, 0, 1, 0, 1), (3, 0, 1, 0, 1)]
+    cs = [(2, 9, 1, 1.0), (9, 3, 1, 1.0), None]
+    nodes, conns = genome(rows, cs, 4, 3)
+    cfg = oracle.mutation_config(conn_add=1.0)
+    u, z = _words(1, 4, 3)
+    u[0, 4] = 0
+    u[0, 5] = -(-(3 << 32) // 4)                            # source key 3
+    u[0, 6] = -(-(1 << 32) // 3)                            # target key 2
+    _, co = oracle.mutate(nodes, conns, 1, 1, cfg, u, z, [8])
+    _same(co[0, 2], [3, 2, 1, 0])
