@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
-    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving", "recurrent", "distance"],
+    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving", "recurrent", "distance", "evolve"],
                     default="ant", help="ant: the headline line; the others: the other shapes")
     return ap.parse_args()
 
@@ -460,6 +460,111 @@ def run_distance(args, R=64):
     print(json.dumps(line), flush=True)
 
 
+def run_evolve(args):
+    """One generation of variation for 10000 Ant-shaped genomes in
+    mid-evolution (27 in, 8 out, max 50 nodes / 200 conns): random words and
+    normals (Philox), 10000 crossovers of random parent pairs, mutation with
+    the appendix's Brax settings (node_add 0.2, conn_add 0.4, bias and weight
+    perturbation 0.5 at rates 0.7 / 0.8, replacement 0.1; feedforward
+    check), and the transform of the children (ready for evaluation)."""
+    import torch
+    import oracle
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    pop = W.ant_related_population(0, POP, acyclic=True)
+    d = neat.dims(I, O, NMAX, CMAX)
+    nodes = torch.from_numpy(pop.nodes).to(dev)
+    conns = torch.from_numpy(pop.conns).to(dev)
+    rng = np.random.default_rng(5)
+    parents_h = rng.integers(0, POP, size=(POP, 2)).astype(np.int32)
+    parents = torch.from_numpy(parents_h).to(dev)
+    Wn, Zn = neat.neat_mutation_sizes(d)
+    xwords = torch.empty((POP, NMAX + CMAX), dtype=torch.int32, device=dev)
+    mwords = torch.empty((POP, Wn), dtype=torch.int32, device=dev)
+    normals = torch.empty((POP, Zn), device=dev)
+    keys = torch.arange(1000, 1000 + POP, dtype=torch.int32, device=dev)
+    child_n = torch.empty_like(nodes)
+    child_c = torch.empty_like(conns)
+    rec = torch.empty(neat.neat_transformed_bytes(POP, d), dtype=torch.uint8, device=dev)
+    status = torch.empty(POP, dtype=torch.int32, device=dev)
+    cfg = neat.mutation(node_add=0.2, conn_add=0.4, bias_init_std=1.0, bias_mutate_power=0.5, bias_mutate_rate=0.7,
+                        bias_replace_rate=0.1, weight_init_std=1.0, weight_mutate_power=0.5, weight_mutate_rate=0.8,
+                        weight_replace_rate=0.1)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    gen = [0]
+
+    def step(record=False):
+        g = gen[0]
+        gen[0] += 1
+        if record:
+            ev[0].record(stream)
+        neat.neat_fill_words(11, 3 * g, xwords, stream=stream)
+        neat.neat_fill_words(11, 3 * g + 1, mwords, stream=stream)
+        neat.neat_fill_normal(11, g, normals, stream=stream)
+        if record:
+            ev[1].record(stream)
+        neat.neat_crossover(nodes, conns, d, parents, xwords, child_n, child_c, stream=stream)
+        if record:
+            ev[2].record(stream)
+        neat.neat_mutate(child_n, child_c, d, cfg, mwords, normals, keys, stream=stream)
+        if record:
+            ev[3].record(stream)
+        neat.neat_transform(child_n, child_c, d, rec, status, stream=stream)
+        if record:
+            ev[4].record(stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ms = timed_events(step, args.steps, stream)
+    parts = []
+    for _ in range(5):
+        step(record=True)
+        torch.cuda.synchronize()
+        parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    comp = {k: statistics.median(p[i] for p in parts)
+            for i, k in enumerate(("random_inputs", "crossover", "mutate", "transform"))}
+    assert (status.cpu().numpy() & 0xFF == 0).all(), "children must stay valid and acyclic"
+    t = statistics.median(ms) / 1e3
+    # the mutation kernel's bytes: the children's tensors read and written, its random inputs read
+    mut_bytes = 2 * (child_n.numel() + child_c.numel()) * 4 + (mwords.numel() + normals.numel()) * 4
+    peak, src = measured_peaks()
+    achieved = mut_bytes / (comp["mutate"] / 1e3) / 1e9
+    # FP64 oracle on a bounded sample: crossover + mutation, one host thread
+    idx = np.arange(0, POP, 20)
+    xw = xwords[idx].cpu().numpy().view(np.uint32)
+    mw = mwords[idx].cpu().numpy().view(np.uint32)
+    zz = normals[idx].cpu().numpy()
+    t0 = time.perf_counter()
+    cn, cc = oracle.crossover(pop.nodes, pop.conns, parents_h[idx], xw)
+    oracle.mutate(cn, cc, I, O, oracle.mutation_config(node_add=0.2, conn_add=0.4, bias_init_std=1.0,
+                                                       bias_mutate_power=0.5, bias_mutate_rate=0.7,
+                                                       bias_replace_rate=0.1, weight_init_std=1.0,
+                                                       weight_mutate_power=0.5, weight_mutate_rate=0.8,
+                                                       weight_replace_rate=0.1),
+                  mw, zz, np.arange(idx.size) + 1000)
+    dt = time.perf_counter() - t0
+    line = {"metric": "genomes/s through one generation of variation (10000 Ant-shaped genomes: random inputs, "
+                      "crossover, mutation, transform)",
+            "value": POP / t, "unit": "genomes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "evolve", "l2": "no flush: the 2 x 36 MB of parent and child tensors stay "
+                                                  "L2-resident within a generation"},
+            "components_ms": comp,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "note": "mutation kernel: child tensors read + written and its random inputs read; "
+                                 "one block per genome runs the structural steps with block barriers, so it is "
+                                 "latency-bound"},
+            "cpu_baseline": {"value": idx.size / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{idx.size} children: crossover + mutation, FP64 C oracle, one thread "
+                                       f"(transform not included)"},
+            "clocks": clocks.summary(), "gpu_launches": 6 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, n_requests=400, n_templates=16):
     """Serving: a Poisson stream (200 requests/s) of requests with log-uniform
     population (64-4096), max nodes (8-512) and batch (1-256), 100 steps each,
@@ -544,6 +649,9 @@ def main():
         return
     if args.workload == "distance":
         run_distance(args)
+        return
+    if args.workload == "evolve":
+        run_evolve(args)
         return
     import torch
     rank, local_rank, world = dist_env()

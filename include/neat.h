@@ -354,6 +354,96 @@ NEAT_API int neat_distance(const void *genes_a, int32_t pop_a, const void *genes
 NEAT_API int neat_speciate(const float *distances_dev, int32_t pop, int32_t n_reps, int64_t ld, float threshold,
                            int32_t *species_dev, void *stream);
 
+/* --------------------------------------------- mutation and crossover
+ *
+ * Tensorized NEAT operators (Section 3.2: node addition writes the first NaN
+ * row, removal writes NaN over a row, attribute modification overwrites a
+ * column; mutation and crossover are built from these), applied to a whole
+ * population.  The paper lists the hyperparameters (below) but no algorithm;
+ * this library's rules:
+ *   Random numbers are inputs.  Per genome, `words` uint32 [W] and `normals`
+ *   f32 [Z] (sizes from neat_mutation_sizes):
+ *     words 0..8 structural: 0 node-addition decision, 1 its connection;
+ *       2 node-deletion decision, 3 its node; 4 connection-addition
+ *       decision, 5 its source, 6 its target; 7 connection-deletion
+ *       decision, 8 its connection;
+ *     node row r: words 16 + 6r + {0 bias, 1 response, 2 activation
+ *       decision, 3 activation choice, 4 aggregation decision, 5 aggregation
+ *       choice}; connection row c: words 16 + 6 max_nodes + 2c + {0 weight,
+ *       1 enabled};
+ *     normals: 0 the new connection's weight; node row r: 4 + 2r + {0 bias,
+ *       1 response}; connection row c: 4 + 2 max_nodes + c.
+ *   A decision with rate p happens when word < T(p) = min(floor(p 2^32), 2^32)
+ *   (computed in double); a choice among k candidates (in row order) takes
+ *   index floor(word k / 2^32).
+ *   Present rows: node key not NaN; connection in, out, enabled not NaN.
+ *   Structural steps, in order:
+ *     1. node addition: a present enabled connection is disabled; the first
+ *        free node row gets (new_keys[g], bias_init_mean, response_init_mean,
+ *        aggregation_default, activation_default); the first free connection
+ *        row (in, new, 1, 1.0) and the next (new, out, 1, old weight).
+ *        Skipped without a free node row, two free connection rows, or when
+ *        the new key is already present.
+ *     2. node deletion: a present node with key >= I + O and every present
+ *        connection touching its key become NaN rows.
+ *     3. connection addition: source among present nodes, target among
+ *        present nodes with key >= I.  An existing present (source, target)
+ *        row is enabled instead; with `feedforward`, a self-loop or a target
+ *        from which the source is reachable through present connections
+ *        between present nodes is rejected; otherwise the first free row gets
+ *        (source, target, 1, weight_init_mean + weight_init_std * normal).
+ *     4. connection deletion: a present connection becomes a NaN row.
+ *   Attribute step, every present row afterwards (node rows with key >= I):
+ *     value: word < T(mutate_rate) -> value + mutate_power * normal,
+ *            else word < T(mutate_rate + replace_rate) -> init_mean + init_std * normal
+ *     (bias, response, weight); activation / aggregation: decision <
+ *     T(replace_rate) -> options[choice]; enabled flips when its word <
+ *     T(enabled_mutate_rate).
+ *   Arithmetic in float with one rounding (fused multiply-add).  Genomes
+ *   must have valid keys (exact integers below 2^24). */
+typedef struct {
+    float node_add, node_delete, conn_add, conn_delete;
+    float bias_init_mean, bias_init_std, bias_mutate_power, bias_mutate_rate, bias_replace_rate;
+    float response_init_mean, response_init_std, response_mutate_power, response_mutate_rate, response_replace_rate;
+    float weight_init_mean, weight_init_std, weight_mutate_power, weight_mutate_rate, weight_replace_rate;
+    float activation_replace_rate, aggregation_replace_rate, enabled_mutate_rate;
+    int32_t activation_default, aggregation_default;
+    int32_t n_activation_options, n_aggregation_options;   /* <= 8, <= 4 */
+    int32_t activation_options[8], aggregation_options[4];
+    int32_t feedforward;                                   /* reject connections that close a cycle */
+} neat_mutation;
+
+/* Random inputs per genome for neat_mutate: *words uint32, *normals float. */
+NEAT_API int neat_mutation_sizes(neat_dims d, int64_t *words, int64_t *normals);
+
+/* Mutate `pop` genomes in place (nodes f32 [pop][max_nodes][5], conns f32
+ * [pop][max_conns][4], 16-byte aligned, device) with the rules above; words
+ * uint32 [pop][W], normals f32 [pop][Z], new_keys int32 [pop] (the key a node
+ * addition gives its node; unique per genome is the caller's choice).
+ * Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat_dims d, const neat_mutation *m,
+                         const uint32_t *words_dev, const float *normals_dev, const int32_t *new_keys_dev,
+                         void *stream);
+
+/* Crossover: child k of parents (parents_dev[2k], parents_dev[2k+1]), the
+ * first the fitter, is the first parent's tensors, except that a present row
+ * whose node key (connection (in, out) pair) is also present in the second
+ * parent takes the second parent's attributes (node: bias, response,
+ * aggregation, activation; connection: enabled, weight; its lowest such row)
+ * when words_dev[k][row] (words_dev[k][max_nodes + row] for connections),
+ * uint32 [n_children][max_nodes + max_conns], is >= 2^31.  Outputs
+ * [n_children][...] must not overlap the inputs.  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_crossover(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
+                            const int32_t *parents_dev, int32_t n_children, const uint32_t *words_dev,
+                            float *nodes_out_dev, float *conns_out_dev, void *stream);
+
+/* Random words for the operators: words_dev[e] (e < n) = component e mod 4
+ * of Philox-4x32-10 (Salmon et al., SC 2011) with key `seed` applied to the
+ * counter (e / 4 low 32 bits, e / 4 high 32 bits, stream low 32 bits,
+ * stream high 32 bits xor 0x574f5244); distinct `stream` values give
+ * independent sequences.  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_fill_words(uint64_t seed, uint64_t stream, uint32_t *words_dev, int64_t n, void *stream_handle);
+
 /* ---------------------------------------------------------- CPPN query
  *
  * CPPN / HyperNEAT extension (Section 4.3): each genome is a CPPN with the

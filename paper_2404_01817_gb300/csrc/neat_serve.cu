@@ -103,6 +103,26 @@ __global__ void gen_normals_kernel(const GenDesc *__restrict__ descs, int nd)
     }
 }
 
+// Raw Philox words: word e = component e mod 4 of the block for counter
+// (e / 4 low, e / 4 high, stream low, stream high ^ 0x574f5244), key = seed.
+__global__ void gen_words_kernel(uint32_t *out, uint64_t n, uint64_t seed, uint64_t stream)
+{
+    const uint64_t blocks = (n + 3) >> 2;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < blocks;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        const U4 r = philox4x32_10(U4{(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)stream,
+                                      (uint32_t)(stream >> 32) ^ 0x574f5244u},
+                                   (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t e = b << 2;
+        if (e + 3 < n) {
+            out[e] = r.x; out[e + 1] = r.y; out[e + 2] = r.z; out[e + 3] = r.w;
+        } else {
+            const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+            for (uint64_t k = 0; e + k < n; ++k) out[e + k] = v[k];
+        }
+    }
+}
+
 __global__ void fill_identity(int32_t *idx, int n)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
@@ -621,5 +641,19 @@ extern "C" int neat_fill_normal(uint64_t seed, int32_t step, int64_t count, floa
     cudaFreeAsync(dd, as_stream(stream));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_fill_normal: launch");
+    return NEAT_OK;
+}
+
+extern "C" int neat_fill_words(uint64_t seed, uint64_t stream, uint32_t *words_dev, int64_t n, void *s)
+{
+    clear_error();
+    if (n < 0) return invalid("neat_fill_words: n < 0");
+    if (n == 0) return NEAT_OK;
+    if (!words_dev) return invalid("neat_fill_words: null pointer");
+    const uint64_t blocks = ((uint64_t)n + 3) / 4;
+    const unsigned grid = (unsigned)std::min<uint64_t>((blocks + 255) / 256, 152u * 16u);
+    gen_words_kernel<<<grid, 256, 0, as_stream(s)>>>(words_dev, (uint64_t)n, seed, stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_fill_words: launch");
     return NEAT_OK;
 }

@@ -87,6 +87,39 @@ class ServeStats(ctypes.Structure):
                 ("ticks", _i64), ("pool_used_bytes", ctypes.c_uint64)]
 
 
+class Mutation(ctypes.Structure):
+    """neat_mutation: the operator hyperparameters (see include/neat.h)."""
+    _fields_ = [(n, ctypes.c_float) for n in (
+        "node_add", "node_delete", "conn_add", "conn_delete",
+        "bias_init_mean", "bias_init_std", "bias_mutate_power", "bias_mutate_rate", "bias_replace_rate",
+        "response_init_mean", "response_init_std", "response_mutate_power", "response_mutate_rate",
+        "response_replace_rate",
+        "weight_init_mean", "weight_init_std", "weight_mutate_power", "weight_mutate_rate", "weight_replace_rate",
+        "activation_replace_rate", "aggregation_replace_rate", "enabled_mutate_rate")] + [
+        ("activation_default", _i32), ("aggregation_default", _i32),
+        ("n_activation_options", _i32), ("n_aggregation_options", _i32),
+        ("activation_options", _i32 * 8), ("aggregation_options", _i32 * 4), ("feedforward", _i32)]
+
+
+def mutation(**kw) -> Mutation:
+    """A Mutation with every rate 0, tanh / sum defaults, response 1 and the
+    feedforward check on, then the given fields; activation_options and
+    aggregation_options as lists."""
+    m = Mutation()
+    m.response_init_mean = 1.0
+    m.activation_default, m.aggregation_default, m.feedforward = 1, 0, 1
+    acts = kw.pop("activation_options", [1])
+    aggs = kw.pop("aggregation_options", [0])
+    m.n_activation_options, m.n_aggregation_options = len(acts), len(aggs)
+    for i, a in enumerate(acts):
+        m.activation_options[i] = a
+    for i, a in enumerate(aggs):
+        m.aggregation_options[i] = a
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return m
+
+
 class PlanOptions(ctypes.Structure):
     _fields_ = [("autotune", _i32), ("size_buckets", _i32), ("block_threads", _i32), ("pdl", _i32)]
 
@@ -107,6 +140,10 @@ _sig = {
     "neat_distance": (ctypes.c_int, [_P, _i32, _P, _i32, Dims, ctypes.c_float, ctypes.c_float, _P, ctypes.c_int64,
                                      _P]),
     "neat_speciate": (ctypes.c_int, [_P, _i32, _i32, ctypes.c_int64, ctypes.c_float, _P, _P]),
+    "neat_mutation_sizes": (ctypes.c_int, [Dims, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "neat_mutate": (ctypes.c_int, [_P, _P, _i32, Dims, ctypes.POINTER(Mutation), _P, _P, _P, _P]),
+    "neat_crossover": (ctypes.c_int, [_P, _P, _i32, Dims, _P, _i32, _P, _P, _P, _P]),
+    "neat_fill_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, _P, _i64, _P]),
     "neat_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
@@ -309,6 +346,51 @@ def neat_speciate(distances, threshold: float, n_reps: int | None = None, specie
     _check(_lib.neat_speciate(_ptr(distances), pop, reps, distances.stride(0), threshold, _ptr(species),
                               _stream(stream)), "neat_speciate")
     return species[:pop]
+
+
+def neat_mutation_sizes(d: Dims) -> tuple[int, int]:
+    """(uint32 words, float normals) of random input per genome for neat_mutate."""
+    w, z = _i64(), _i64()
+    _check(_lib.neat_mutation_sizes(d, ctypes.byref(w), ctypes.byref(z)), "neat_mutation_sizes")
+    return w.value, z.value
+
+
+def neat_mutate(nodes, conns, d: Dims, m: Mutation, words, normals, new_keys, stream=None):
+    """Mutate a population in place (torch CUDA tensors f32 [P][Nmax][5],
+    [P][Cmax][4]); words uint32 (int32 tensor) [P][W], normals f32 [P][Z],
+    new_keys int32 [P]."""
+    import torch
+    pop = nodes.shape[0]
+    W, Z = neat_mutation_sizes(d)
+    assert nodes.is_contiguous() and conns.is_contiguous() and words.is_contiguous() and normals.is_contiguous()
+    assert words.numel() >= pop * W and normals.numel() >= pop * Z and new_keys.numel() >= pop
+    assert words.dtype in (torch.int32, torch.uint32) and normals.dtype == torch.float32
+    assert new_keys.dtype == torch.int32
+    _check(_lib.neat_mutate(_ptr(nodes), _ptr(conns), pop, d, ctypes.byref(m), _ptr(words), _ptr(normals),
+                            _ptr(new_keys), _stream(stream)), "neat_mutate")
+    return nodes, conns
+
+
+def neat_crossover(nodes, conns, d: Dims, parents, words, nodes_out=None, conns_out=None, stream=None):
+    """Children of parent pairs (int32 [K][2], the first the fitter); words
+    uint32 (int32 tensor) [K][Nmax + Cmax].  Returns (nodes_out, conns_out)."""
+    import torch
+    K = parents.shape[0]
+    if nodes_out is None:
+        nodes_out = torch.empty((K, d.max_nodes, 5), dtype=torch.float32, device=nodes.device)
+    if conns_out is None:
+        conns_out = torch.empty((K, d.max_conns, 4), dtype=torch.float32, device=nodes.device)
+    assert parents.dtype == torch.int32 and parents.is_contiguous() and words.is_contiguous()
+    assert words.numel() >= K * (d.max_nodes + d.max_conns)
+    _check(_lib.neat_crossover(_ptr(nodes), _ptr(conns), nodes.shape[0], d, _ptr(parents), K, _ptr(words),
+                               _ptr(nodes_out), _ptr(conns_out), _stream(stream)), "neat_crossover")
+    return nodes_out, conns_out
+
+
+def neat_fill_words(seed: int, stream_id: int, out, stream=None):
+    """Fill an int32/uint32 tensor with Philox words (see include/neat.h)."""
+    _check(_lib.neat_fill_words(seed, stream_id, _ptr(out), out.numel(), _stream(stream)), "neat_fill_words")
+    return out
 
 
 def neat_forward(transformed, pop: int, d: Dims, inputs, outputs=None, launch: Launch | None = None,

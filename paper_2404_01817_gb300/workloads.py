@@ -362,14 +362,19 @@ def ant_recurrent_population(seed: int = 0, pop: int = 10000) -> Population:
 def related_population(seed: int, pop: int, num_inputs: int, num_outputs: int, max_nodes: int, max_conns: int,
                        ancestor_hidden: int, ancestor_edges: int, new_nodes: int, new_conns: int,
                        key_pool: int, p_perturb: float = 0.8, sigma: float = 0.5, p_flip: float = 0.05,
-                       p_drop: float = 0.1, p_act: float = 0.05, stream: int = 30) -> Population:
+                       p_drop: float = 0.1, p_act: float = 0.05, stream: int = 30,
+                       acyclic: bool = False) -> Population:
     """A population in mid-evolution, for genome distances: mutated copies of
     one random ancestor DAG.  Each member perturbs weights and biases
     (N(0, sigma), probability p_perturb), flips enabled flags (p_flip), drops
     connections (p_drop), changes activations (p_act), and adds up to
     `new_nodes` hidden nodes whose keys come from a shared pool of `key_pool`
     keys (so added genes are often homologous across members) and up to
-    `new_conns` connections between present nodes.  Rows are shuffled."""
+    `new_conns` connections between present nodes.  Rows are shuffled.
+    acyclic: every key gets one place in a global order (the ancestor's
+    topological order, pool keys at random places) and added connections
+    only run forward in it, so every member stays a DAG (disabled
+    connections included)."""
     I, O = num_inputs, num_outputs
     anc = random_dag_population(seed, 1, I, O, max_nodes, max_conns, hidden=lambda r: ancestor_hidden,
                                 edges=lambda r, n: ancestor_edges, acts=ALL_ACTS, aggs=ALL_AGGS,
@@ -377,6 +382,27 @@ def related_population(seed: int, pop: int, num_inputs: int, num_outputs: int, m
     an = anc.nodes[0][~np.isnan(anc.nodes[0, :, 0])]
     ac = anc.conns[0][~np.isnan(anc.conns[0, :, 0])]
     base_key = int(an[:, 0].max()) + 1
+    place = {}
+    if acyclic:
+        # the ancestor's topological order over all its connections (Kahn)
+        indeg = {int(k): 0 for k in an[:, 0]}
+        for a_, b_ in ac[:, :2].astype(np.int64):
+            indeg[int(b_)] += 1
+        ready = sorted(k for k, v in indeg.items() if v == 0)
+        while ready:
+            k = ready.pop(0)
+            place[k] = float(len(place))
+            for a_, b_ in ac[:, :2].astype(np.int64):
+                if int(a_) == k:
+                    indeg[int(b_)] -= 1
+                    if indeg[int(b_)] == 0:
+                        ready.append(int(b_))
+        assert len(place) == len(indeg)
+        prng = rng_for(seed, stream + 2)
+        for j in range(key_pool):
+            place[base_key + j] = float(prng.uniform(-0.5, len(indeg) - 0.5))
+        for k in range(num_inputs):
+            place[k] = -1.0 - k
     P = empty_population(pop, max_nodes, max_conns, I, O)
     for g in range(pop):
         rng = rng_for(seed, stream + 1, g)
@@ -409,6 +435,8 @@ def related_population(seed: int, pop: int, num_inputs: int, num_outputs: int, m
             if len(add) >= want:
                 break
             pair = (int(rng.choice(present)), int(rng.choice(targets)))
+            if acyclic and not place[pair[0]] < place[pair[1]]:
+                continue
             if pair not in have:
                 have.add(pair)
                 add.append((pair[0], pair[1], 1.0, float(rng.standard_normal())))
@@ -419,9 +447,9 @@ def related_population(seed: int, pop: int, num_inputs: int, num_outputs: int, m
     return P
 
 
-def ant_related_population(seed: int = 0, pop: int = 10000) -> Population:
+def ant_related_population(seed: int = 0, pop: int = 10000, acyclic: bool = False) -> Population:
     """Ant-shaped population in mid-evolution (27 in, 8 out, max 50 nodes /
     200 conns): an ancestor with 8 hidden nodes and 120 connections, members
     adding up to 7 nodes from a pool of 20 keys and up to 30 connections."""
     return related_population(seed, pop, 27, 8, 50, 200, ancestor_hidden=8, ancestor_edges=120, new_nodes=7,
-                              new_conns=30, key_pool=20)
+                              new_conns=30, key_pool=20, acyclic=acyclic)
