@@ -226,3 +226,20 @@ def crossover(nodes, conns, parents, words):
         [ctypes.c_void_p] * 3
     L.oracle_crossover(_ptr(nodes), _ptr(conns), N, C, _ptr(parents), K, _ptr(words), _ptr(no), _ptr(co))
     return no, co
+
+
+def substrate_forward(weights, inputs, hidden_act: int = 1, output_act: int = 1):
+    """HyperNEAT substrate outputs (double [P][B][R]) from CPPN weight blocks
+    f32 [P][L-1][R][R] (source-major) and inputs f32 [P][B][R]."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    x = np.ascontiguousarray(inputs, dtype=np.float32)
+    P, Lm1, R = w.shape[0], w.shape[1], w.shape[2]
+    assert w.shape == (P, Lm1, R, R) and x.shape[0] == P and x.shape[2] == R
+    B = x.shape[1]
+    out = np.empty((P, B, R), np.float64)
+    L = lib()
+    L.oracle_substrate_forward.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p]
+    L.oracle_substrate_forward(_ptr(w), P, R, Lm1 + 1, _ptr(x), B, hidden_act, output_act, _ptr(out))
+    return out

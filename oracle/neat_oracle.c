@@ -959,3 +959,36 @@ int oracle_crossover(const float *nodes, const float *conns, int N, int C, const
     }
     return 0;
 }
+
+/*
+ * HyperNEAT substrate evaluation (Section 4.3 extensions: the CPPN's
+ * thresholded weights define a layered substrate network).  The paper gives
+ * no substrate rule; this oracle fixes: layer 0 holds the R = res^2 inputs of
+ * one input vector, and layer l+1 node t = act(sum_s W_l[s][t] v_l[s]) with
+ * W_l the weight block l of the CPPN query (weights[genome][l][s][t]); no
+ * bias; act = hidden_act for the inner layers and output_act for the last.
+ * Plain loops in double.
+ */
+int oracle_substrate_forward(const float *weights, int P, int R, int L, const float *inputs, int B,
+                             int hidden_act, int output_act, double *out)
+{
+    double *cur = malloc(sizeof(double) * (size_t)R), *nxt = malloc(sizeof(double) * (size_t)R);
+    for (int g = 0; g < P; g++)
+        for (int b = 0; b < B; b++) {
+            const float *x = inputs + ((size_t)g * B + b) * R;
+            for (int s = 0; s < R; s++) cur[s] = x[s];
+            for (int l = 0; l + 1 < L; l++) {
+                const float *Wl = weights + ((size_t)g * (L - 1) + l) * (size_t)R * R;
+                const int act = (l + 2 == L) ? output_act : hidden_act;
+                for (int t = 0; t < R; t++) {
+                    double acc = 0.0;
+                    for (int s = 0; s < R; s++) acc += (double)Wl[(size_t)s * R + t] * cur[s];
+                    nxt[t] = act_fn(act, acc);
+                }
+                double *tmp = cur; cur = nxt; nxt = tmp;
+            }
+            for (int t = 0; t < R; t++) out[((size_t)g * B + b) * R + t] = cur[t];
+        }
+    free(cur); free(nxt);
+    return 0;
+}

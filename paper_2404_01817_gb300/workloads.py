@@ -453,3 +453,15 @@ def ant_related_population(seed: int = 0, pop: int = 10000, acyclic: bool = Fals
     adding up to 7 nodes from a pool of 20 keys and up to 30 connections."""
     return related_population(seed, pop, 27, 8, 50, 200, ancestor_hidden=8, ancestor_edges=120, new_nodes=7,
                               new_conns=30, key_pool=20, acyclic=acyclic)
+
+
+def substrate_weights(seed: int, pop: int, res: int = 16, layers: int = 3, scale: float = 0.25,
+                      threshold: float = 0.2) -> np.ndarray:
+    """Weight blocks shaped like a thresholded CPPN query (f32
+    [pop][layers-1][res^2][res^2], source-major): N(0, scale) values with
+    |w| < threshold set to 0 (about 58% zeros at the defaults)."""
+    rng = rng_for(seed, 40)
+    R = res * res
+    w = (scale * rng.standard_normal((pop, layers - 1, R, R))).astype(np.float32)
+    w[np.abs(w) < threshold] = 0.0
+    return w
