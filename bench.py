@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
-    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving", "recurrent", "distance", "evolve"],
+    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving", "recurrent", "distance", "evolve",
+                                           "substrate"],
                     default="ant", help="ant: the headline line; the others: the other shapes")
     return ap.parse_args()
 
@@ -565,6 +566,68 @@ def run_evolve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_substrate(args, S=50):
+    """HyperNEAT substrate control step: 1000 CPPN genomes' weight blocks
+    (neat_cppn_query, 3 layers of 16 x 16, threshold 0.2; 524 MB resident)
+    evaluated on one N(0,1) input vector per genome per step (tanh hidden and
+    output layers), S steps per timed repetition; the same at 16 vectors per
+    genome is reported beside it."""
+    import torch
+    import oracle
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    P = 1000
+    pop = W.cppn_population(0, P)
+    d = neat.dims(5, 1, pop.max_nodes, pop.max_conns)
+    rec, _ = neat.neat_transform(torch.from_numpy(pop.nodes).to(dev), torch.from_numpy(pop.conns).to(dev), d)
+    w = neat.neat_cppn_query(rec, P, d, 16, 3, 0.2).contiguous()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(21)
+    x1 = torch.randn((S, P, 1, 256), device=dev, generator=gen)
+    y1 = torch.empty_like(x1)
+    x16 = torch.randn((P, 16, 256), device=dev, generator=gen)
+    y16 = torch.empty_like(x16)
+    stream = torch.cuda.current_stream(dev)
+
+    def steps():
+        for s in range(S):
+            neat.neat_substrate_forward(w, x1[s], outputs=y1[s], stream=stream)
+    for _ in range(args.warmup):
+        steps()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ms = timed_events(steps, args.steps, stream)
+    t = statistics.median(ms) / 1e3 / S
+    ms16 = timed_events(lambda: neat.neat_substrate_forward(w, x16, outputs=y16, stream=stream), 10, stream)
+    t16 = statistics.median(ms16) / 1e3
+    wbytes = w.numel() * 4
+    alg = wbytes + 2 * P * 256 * 4                   # weight blocks read once + inputs + outputs
+    peak, src = measured_peaks()
+    achieved = alg / t / 1e9
+    idx = np.arange(0, P, 100)
+    wh = w[idx].cpu().numpy()
+    xh = x1[0, idx].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.substrate_forward(wh, xh)
+    dt = time.perf_counter() - t0
+    line = {"metric": "substrate genome-forwards/s (1000 HyperNEAT substrates, 3 layers of 16 x 16, 1 input "
+                      "vector per genome per step)",
+            "value": P / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "HyperNEAT substrate", "resolution": 16, "layers": 3, "steps_per_rep": S,
+                       "l2": "inputs larger than L2 (524 MB of weight blocks read every step)"},
+            "batch16": {"value": P * 16 / t16, "unit": UNIT, "ms": t16 * 1e3,
+                        "achieved_gbs": (wbytes + 2 * P * 16 * 256 * 4) / t16 / 1e9},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "note": "algorithmic bytes = the weight blocks (read once per step) + inputs + outputs"},
+            "cpu_baseline": {"value": idx.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{idx.size} substrates x 1 vector, FP64 C oracle, one thread"},
+            "clocks": clocks.summary(), "gpu_launches": args.steps * S}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, n_requests=400, n_templates=16):
     """Serving: a Poisson stream (200 requests/s) of requests with log-uniform
     population (64-4096), max nodes (8-512) and batch (1-256), 100 steps each,
@@ -652,6 +715,9 @@ def main():
         return
     if args.workload == "evolve":
         run_evolve(args)
+        return
+    if args.workload == "substrate":
+        run_substrate(args)
         return
     import torch
     rank, local_rank, world = dist_env()

@@ -465,6 +465,19 @@ typedef struct neat_substrate {
 NEAT_API int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_dims d, neat_substrate sub,
                              float threshold, float *weights_dev, void *stream);
 
+/* HyperNEAT substrate evaluation: the layered network that the weight
+ * blocks of neat_cppn_query define (weights f32 [pop][layers-1][R][R],
+ * source-major, R = resolution^2), on inputs f32 [pop][batch][R] (one value
+ * per node of the first layer) -> outputs f32 [pop][batch][R] (the last
+ * layer).  Layer l+1 node t = act(sum_s W_l[s][t] v_l[s]), no bias;
+ * act = hidden_act for inner layers, output_act for the last (ids as for
+ * nodes).  The paper gives no substrate rule; this is this library's.
+ * Float arithmetic, source sums split into at most a fixed number of slices
+ * added in order (deterministic).  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_substrate_forward(const float *weights_dev, int32_t pop, neat_substrate sub, const float *inputs_dev,
+                                    int32_t batch, int32_t hidden_act, int32_t output_act, float *outputs_dev,
+                                    void *stream);
+
 /* ------------------------------------------------------------ batching
  *
  * A plan evaluates several transformed populations -- of different

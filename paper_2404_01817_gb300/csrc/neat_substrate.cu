@@ -1,0 +1,186 @@
+// HyperNEAT substrate evaluation (the CPPN / HyperNEAT extensions of Section
+// 4.3): the weight blocks written by neat_cppn_query define a layered
+// network over the substrate grid, evaluated here for a batch of input
+// vectors per genome: layer 0 = the R = res^2 inputs, layer l+1 node
+// t = act(sum_s W_l[s][t] v_l[s]) (no bias; hidden_act inside, output_act on
+// the last layer).
+//
+// GB300 mapping: for the control setting (one or a few input vectors per
+// genome) this is a batched matrix-vector product whose cost is reading the
+// fp32 weight blocks once from HBM (2 x 256 KB per genome at 16 x 16), so it
+// runs on the FP32 pipes at the bandwidth roofline rather than on tensor
+// cores, which would also round the weights below the float tolerance.  One
+// block per (genome, batch chunk of NB vectors): each thread owns VEC
+// adjacent target columns of one slice of the source range, streams its
+// weight rows with VEC-wide read-only loads (coalesced across the block),
+// keeps NB x VEC accumulators in registers, and the slices are summed in a
+// fixed order through shared memory, where the layer's values also stay, so
+// the result is a function of the inputs alone.
+#include <algorithm>
+
+#include "neat_device.cuh"
+#include "neat_internal.h"
+
+namespace neat {
+namespace {
+
+constexpr int kSubThreads = 256;
+
+struct SubArgs {
+    const float *w;        // [pop][L-1][R][R]
+    const float *x;        // [pop][B][R]
+    float *y;              // [pop][B][R]
+    int R, L, B;
+    int hidden_act, output_act;
+    int groups;            // slices of the source range (threads per column group)
+    int cols;              // column groups per pass (cols * groups <= threads)
+};
+
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<1> {
+    using T = float;
+    static __device__ __forceinline__ float get(const float &v, int) { return v; }
+};
+template <>
+struct VecT<4> {
+    using T = float4;
+    static __device__ __forceinline__ float get(const float4 &v, int i)
+    {
+        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    }
+};
+
+template <int NB, int VEC>
+__global__ void __launch_bounds__(kSubThreads) substrate_kernel(const SubArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int R = a.R;
+    float *cur = sm;                       // [NB][R]
+    float *nxt = cur + NB * R;             // [NB][R]
+    float *part = nxt + NB * R;            // [groups][NB][R]
+    const int g = blockIdx.x, b0 = blockIdx.y * NB;
+    const int nb = min(NB, a.B - b0);
+    const int tid = threadIdx.x;
+    const float *xg = a.x + ((size_t)g * a.B + b0) * R;
+    for (int i = tid; i < NB * R; i += kSubThreads) cur[i] = (i < nb * R) ? __ldg(xg + i) : 0.0f;
+    __syncthreads();
+    const int ncols = R / VEC;                              // column groups in a row
+    const int slice = (R + a.groups - 1) / a.groups;        // sources per slice
+    const int col_in_pass = tid % a.cols, grp = tid / a.cols;
+    using V = typename VecT<VEC>::T;
+    for (int l = 0; l + 1 < a.L; ++l) {
+        const float *Wl = a.w + ((size_t)g * (a.L - 1) + l) * (size_t)R * R;
+        const int act = (l + 2 == a.L) ? a.output_act : a.hidden_act;
+        for (int c0 = 0; c0 < ncols; c0 += a.cols) {
+            const int c = c0 + col_in_pass;
+            if (grp < a.groups && c < ncols) {
+                float acc[NB][VEC];
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[b][v] = 0.0f;
+                const int s0 = grp * slice, s1 = min(R, s0 + slice);
+                const V *col = reinterpret_cast<const V *>(Wl) + c;
+#pragma unroll 8
+                for (int s = s0; s < s1; ++s) {
+                    const V wv = __ldg(col + (size_t)s * ncols);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float xv = cur[b * R + s];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[b][v] = fmaf(xv, VecT<VEC>::get(wv, v), acc[b][v]);
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) part[((size_t)grp * NB + b) * R + c * VEC + v] = acc[b][v];
+            }
+            __syncthreads();
+            // sum the slices in order, apply the activation
+            for (int i = tid; i < NB * a.cols * VEC; i += kSubThreads) {
+                const int b = i / (a.cols * VEC), t = c0 * VEC + i % (a.cols * VEC);
+                if (t >= R) continue;
+                float s = part[(size_t)b * R + t];
+                for (int j = 1; j < a.groups; ++j) s += part[((size_t)j * NB + b) * R + t];
+                nxt[b * R + t] = activate((uint32_t)act, s);
+            }
+            __syncthreads();
+        }
+        float *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    float *yg = a.y + ((size_t)g * a.B + b0) * R;
+    for (int i = tid; i < nb * R; i += kSubThreads) yg[i] = cur[i];
+}
+
+template <int NB, int VEC>
+int launch_sub(const SubArgs &a, int pop, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * ((size_t)2 * NB * a.R + (size_t)a.groups * NB * a.R);
+    auto kern = substrate_kernel<NB, VEC>;
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_substrate_forward: shared memory");
+    if (rc) return rc;
+    const dim3 grid((unsigned)pop, (unsigned)((a.B + NB - 1) / NB));
+    kern<<<grid, kSubThreads, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_substrate_forward: launch");
+    return NEAT_OK;
+}
+
+template <int VEC>
+int launch_vec(const SubArgs &a, int pop, int nb, cudaStream_t s)
+{
+    switch (nb) {
+    case 1: return launch_sub<1, VEC>(a, pop, s);
+    case 2: return launch_sub<2, VEC>(a, pop, s);
+    case 4: return launch_sub<4, VEC>(a, pop, s);
+    case 8: return launch_sub<8, VEC>(a, pop, s);
+    default: return launch_sub<16, VEC>(a, pop, s);
+    }
+}
+
+}  // namespace
+}  // namespace neat
+
+using namespace neat;
+
+extern "C" int neat_substrate_forward(const float *weights_dev, int32_t pop, neat_substrate sub, const float *inputs_dev,
+                                      int32_t batch, int32_t hidden_act, int32_t output_act, float *outputs_dev,
+                                      void *stream)
+{
+    clear_error();
+    if (sub.resolution < 2 || sub.resolution > 181 || sub.layers < 2)
+        return invalid("neat_substrate_forward: substrate resolution must be in 2..181 and layers >= 2");
+    if (pop < 0 || batch < 0) return invalid("neat_substrate_forward: sizes must be >= 0");
+    if (hidden_act < 0 || hidden_act > 6 || output_act < 0 || output_act > 6)
+        return invalid("neat_substrate_forward: activation ids are 0..6");
+    if (pop == 0 || batch == 0) return NEAT_OK;
+    if (!weights_dev || !inputs_dev || !outputs_dev) return invalid("neat_substrate_forward: null pointer");
+    if (pop > 0x7fffffff / 1 || (batch + 15) / 16 > 65535) return invalid("neat_substrate_forward: too many work items");
+    SubArgs a;
+    a.w = weights_dev;
+    a.x = inputs_dev;
+    a.y = outputs_dev;
+    a.R = sub.resolution * sub.resolution;
+    a.L = sub.layers;
+    a.B = batch;
+    a.hidden_act = hidden_act;
+    a.output_act = output_act;
+    const bool vec4 = (a.R % 4 == 0) && (reinterpret_cast<uintptr_t>(weights_dev) % 16 == 0);
+    const int ncols = vec4 ? a.R / 4 : a.R;
+    a.cols = std::min(ncols, kSubThreads);
+    a.groups = std::max(1, kSubThreads / a.cols);
+    int nb = 1;
+    while (nb < batch && nb < 16) nb <<= 1;
+    // shared memory: two value tiles and the slice partials
+    while (sizeof(float) * ((size_t)2 * nb * a.R + (size_t)a.groups * nb * a.R) > 200u * 1024u && a.groups > 1)
+        a.groups >>= 1;
+    while (sizeof(float) * ((size_t)2 * nb * a.R + (size_t)a.groups * nb * a.R) > 200u * 1024u && nb > 1) nb >>= 1;
+    if (sizeof(float) * ((size_t)3 * nb * a.R) > 200u * 1024u)
+        return invalid("neat_substrate_forward: substrate too large for one block");
+    return vec4 ? launch_vec<4>(a, pop, nb, as_stream(stream)) : launch_vec<1>(a, pop, nb, as_stream(stream));
+}

@@ -144,6 +144,7 @@ _sig = {
     "neat_mutate": (ctypes.c_int, [_P, _P, _i32, Dims, ctypes.POINTER(Mutation), _P, _P, _P, _P]),
     "neat_crossover": (ctypes.c_int, [_P, _P, _i32, Dims, _P, _i32, _P, _P, _P, _P]),
     "neat_fill_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, _P, _i64, _P]),
+    "neat_substrate_forward": (ctypes.c_int, [_P, _i32, Substrate, _P, _i32, _i32, _i32, _P, _P]),
     "neat_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "neat_forward_ex": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.POINTER(Launch), _P]),
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
@@ -385,6 +386,21 @@ def neat_crossover(nodes, conns, d: Dims, parents, words, nodes_out=None, conns_
     _check(_lib.neat_crossover(_ptr(nodes), _ptr(conns), nodes.shape[0], d, _ptr(parents), K, _ptr(words),
                                _ptr(nodes_out), _ptr(conns_out), _stream(stream)), "neat_crossover")
     return nodes_out, conns_out
+
+
+def neat_substrate_forward(weights, inputs, resolution: int = 16, layers: int = 3, hidden_act: int = 1,
+                           output_act: int = 1, outputs=None, stream=None):
+    """HyperNEAT substrate outputs f32 [P][B][R] from CPPN weight blocks
+    f32 [P][layers-1][R][R] and inputs f32 [P][B][R]."""
+    import torch
+    P, B, R = inputs.shape
+    assert R == resolution * resolution and weights.shape == (P, layers - 1, R, R)
+    assert weights.is_contiguous() and inputs.is_contiguous() and inputs.dtype == torch.float32
+    if outputs is None:
+        outputs = torch.empty((P, B, R), dtype=torch.float32, device=inputs.device)
+    _check(_lib.neat_substrate_forward(_ptr(weights), P, Substrate(resolution, layers), _ptr(inputs), B, hidden_act,
+                                       output_act, _ptr(outputs), _stream(stream)), "neat_substrate_forward")
+    return outputs
 
 
 def neat_fill_words(seed: int, stream_id: int, out, stream=None):
