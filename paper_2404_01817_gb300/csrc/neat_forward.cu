@@ -107,7 +107,7 @@ __device__ __forceinline__ void walk_serial(const uint4 *srec, float *v, int npo
         }
         const float a = agg_combine(agg, agg_combine(agg, q0, q1), agg_combine(agg, q2, q3));
         if (live)
-            v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+            v[p] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                         : node_output(ne, agg, act, ec, a);
     }
 }

@@ -119,7 +119,7 @@ __device__ __forceinline__ void eval_node(const uint4 ne, const uint2 *__restric
     const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
     const uint32_t ec = ne.z >> 16;
     const float a = partials<T1, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, lgT, col, 0, 4);
-    v[vslot<T1>(p, lgT, col)] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+    v[vslot<T1>(p, lgT, col)] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                                      : node_output(ne, agg, act, ec, a);
 }
 
@@ -171,7 +171,7 @@ __device__ __forceinline__ void walk_levels(const uint4 *srec, float *v, int G, 
                     const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
                     const uint32_t ec = ne.z >> 16;
                     const float a = partials<true, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, 0, 0, 0, 4);
-                    v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                    v[p] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                                 : node_output(ne, agg, act, ec, a);
                 }
                 const int pn = p1 + lane;
@@ -203,7 +203,7 @@ __device__ __forceinline__ void walk_levels(const uint4 *srec, float *v, int G, 
                 float a = partials<true, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, 0, 0, part * nk, nk);
                 for (int m = 1; m < split; m <<= 1) a = agg_combine(agg, a, __shfl_xor_sync(mask, a, m));
                 if (part == 0)
-                    v[p] = FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                    v[p] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                                 : node_output(ne, agg, act, ec, a);
             }
             p0 = p1;

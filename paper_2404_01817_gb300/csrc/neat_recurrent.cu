@@ -47,7 +47,7 @@ __device__ __forceinline__ float *rnn_iterate(const uint4 *srec, float *cur, flo
                 const uint32_t ec = ne.z >> 16;
                 const float a = partials<T1, FAST>(agg, edges + (ne.z & 0xffffu), ec, cur, lgT, col, 0, 4);
                 nxt[vslot<T1>(p, lgT, col)] =
-                    FAST ? tanhf(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                    FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                          : node_output(ne, agg, act, ec, a);
             }
         }

@@ -296,3 +296,22 @@ def test_schedule_order_is_a_permutation_and_changes_nothing(neat):
                 np.testing.assert_array_equal(ys[s].cpu().numpy(),
                                               neat.neat_forward(rec, pop.pop, d, xs[s].contiguous()).cpu().numpy())
             cache.close()
+
+
+def test_node_tanh_error_bound(neat):
+    """The nodes' tanh (1 - 2 / (exp(2z) + 1) on the hardware exponential and
+    reciprocal) through the public path: one tanh node y = tanh(x), against
+    numpy's double tanh; absolute error <= 5e-7, limits and NaN exact."""
+    nodes, conns = genome([(0, 0, 1, 0, 0), (1, 0, 1, 0, 1)], [(0, 1, 1, 1.0)])
+    x = np.concatenate([np.linspace(-12, 12, 200001), np.linspace(-1e-3, 1e-3, 2001), 10.0 ** np.arange(-30, 3),
+                        -(10.0 ** np.arange(-30, 3)), [0.0, 40.0, -40.0, 1e30, -1e30, np.inf, -np.inf]])
+    x = x.astype(np.float32)
+    X = x.reshape(1, -1, 1)
+    d = neat.dims(1, 1, 2, 1)
+    rec, st = neat.neat_transform(_dev(nodes), _dev(conns), d)
+    y = neat.neat_forward(rec, 1, d, _dev(X)).cpu().numpy().ravel()
+    ref = np.tanh(x.astype(np.float64))
+    assert np.max(np.abs(y - ref)) <= 5e-7
+    assert (y[x >= 20] == 1.0).all() and (y[x <= -20] == -1.0).all()
+    xn = np.array([[[np.nan]]], np.float32)
+    assert np.isnan(neat.neat_forward(rec, 1, d, _dev(xn)).cpu().numpy()).all()
