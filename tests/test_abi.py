@@ -66,3 +66,41 @@ def test_argument_errors_do_not_touch_the_device(lib_path):
     bad = neat.Launch(3, 1, 1, 0)
     assert lib.neat_forward_ex(16, 1, d, 16, 1, 16, ctypes.byref(bad), None) == neat.NEAT_EINVAL
     assert lib.neat_transform(None, None, 0, d, None, 0, None, None) == neat.NEAT_OK   # empty population
+
+
+def test_argument_errors_of_the_other_entry_points(lib_path):
+    """Sizes and argument checks of the recurrent, distance, evolve and
+    substrate entry points, all answered on the host."""
+    from paper_2404_01817_gb300 import neat
+    lib = neat._lib
+    d = neat.dims(27, 8, 50, 200)
+    # sizes
+    assert neat.neat_gene_stride(d) % 128 == 0
+    assert neat.neat_gene_stride(d) >= 16 + 4 * 50 + 16 * 50 + 16 * 200
+    assert neat.neat_gene_stride(neat.dims(0, 1, 1025, 4)) == 0
+    assert neat.neat_mutation_sizes(d) == (16 + 6 * 50 + 2 * 200, 4 + 2 * 50 + 200)
+    # empty work is a no-op, bad sizes and null pointers are NEAT_EINVAL
+    assert lib.neat_transform_recurrent(None, None, 0, d, None, 0, None, None) == neat.NEAT_OK
+    assert lib.neat_transform_recurrent(None, None, 4, d, None, 0, None, None) == neat.NEAT_EINVAL
+    assert lib.neat_forward_recurrent(16, 1, d, 16, 1, -1, 16, None) == neat.NEAT_EINVAL
+    assert lib.neat_distance_prepare(None, None, 0, d, None, 0, None, None) == neat.NEAT_OK
+    assert lib.neat_distance_prepare(None, None, 3, d, None, 0, None, None) == neat.NEAT_EINVAL
+    assert lib.neat_distance(16, 4, 16, 0, d, ctypes.c_float(1.0), ctypes.c_float(0.5), 16, 0, None) == neat.NEAT_OK
+    assert lib.neat_distance(16, 4, 16, 5, d, ctypes.c_float(1.0), ctypes.c_float(0.5), 16, 4, None) \
+        == neat.NEAT_EINVAL                                                   # ld_out < pop_b
+    assert lib.neat_distance(16, 4, 24, 5, d, ctypes.c_float(1.0), ctypes.c_float(0.5), 16, 5, None) \
+        == neat.NEAT_EINVAL                                                   # misaligned records
+    assert lib.neat_speciate(16, 4, 8, 4, ctypes.c_float(3.0), 16, None) == neat.NEAT_EINVAL   # ld < n_reps
+    assert lib.neat_speciate(None, 0, 8, 8, ctypes.c_float(3.0), None, None) == neat.NEAT_OK
+    m = neat.mutation(node_add=0.2)
+    assert lib.neat_mutate(None, None, 0, d, ctypes.byref(m), None, None, None, None) == neat.NEAT_OK
+    assert lib.neat_mutate(16, 16, 2, d, ctypes.byref(m), None, 16, 16, None) == neat.NEAT_EINVAL
+    m.n_activation_options = 9
+    assert lib.neat_mutate(16, 16, 2, d, ctypes.byref(m), 16, 16, 16, None) == neat.NEAT_EINVAL
+    assert lib.neat_crossover(16, 16, 4, d, 16, 0, 16, 16, 16, None) == neat.NEAT_OK
+    assert lib.neat_crossover(16, 24, 4, d, 16, 2, 16, 16, 16, None) == neat.NEAT_EINVAL   # misaligned conns
+    assert lib.neat_fill_words(1, 2, None, 0, None) == neat.NEAT_OK
+    assert lib.neat_fill_words(1, 2, None, 8, None) == neat.NEAT_EINVAL
+    assert lib.neat_substrate_forward(16, 4, neat.Substrate(1, 3), 16, 1, 1, 1, 16, None) == neat.NEAT_EINVAL
+    assert lib.neat_substrate_forward(16, 4, neat.Substrate(16, 3), 16, 1, 9, 1, 16, None) == neat.NEAT_EINVAL
+    assert lib.neat_substrate_forward(None, 0, neat.Substrate(16, 3), None, 1, 1, 1, None, None) == neat.NEAT_OK
