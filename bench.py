@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
-    ap.add_argument("--workload", choices=["ant", "batched", "cppn", "serving", "recurrent", "distance", "evolve",
-                                           "substrate"],
+    ap.add_argument("--workload", choices=["ant", "xor", "batched", "cppn", "serving", "recurrent", "distance",
+                                           "evolve", "substrate"],
                     default="ant", help="ant: the headline line; the others: the other shapes")
     return ap.parse_args()
 
@@ -205,6 +205,62 @@ def timed_events(fn, reps, stream):
         b.record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_xor(args, reps=1000):
+    """XOR (100 genomes grown from the 3 -> 1 net, the 4 points with a bias
+    input): latency-bound, so the line reports microseconds per call (CUDA
+    events around each call, p50 / p99 over `reps` calls) for the transform
+    and the forward, and host-to-host latency of both through the public API."""
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    pop = W.xor_population(0, 100)
+    d = neat.dims(3, 1, pop.max_nodes, pop.max_conns)
+    nodes = torch.from_numpy(pop.nodes).to(dev)
+    conns = torch.from_numpy(pop.conns).to(dev)
+    x = torch.from_numpy(W.xor_inputs(100)).to(dev)
+    rec, st = neat.neat_transform(nodes, conns, d)
+    y = neat.neat_forward(rec, 100, d, x)
+    stream = torch.cuda.current_stream(dev)
+    L = neat.neat_default_launch(100, d, 4)
+
+    def per_call(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        t = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
+        return float(np.percentile(t, 50)), float(np.percentile(t, 99))
+    for _ in range(args.warmup):
+        neat.neat_transform(nodes, conns, d, rec, st, stream=stream)
+        neat.neat_forward(rec, 100, d, x, y, launch=L, stream=stream)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        tr = per_call(lambda: neat.neat_transform(nodes, conns, d, rec, st, stream=stream))
+        fw = per_call(lambda: neat.neat_forward(rec, 100, d, x, y, launch=L, stream=stream))
+    xh = x.cpu().pin_memory()
+    yh = torch.empty(y.shape, pin_memory=True)
+    host = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        x.copy_(xh, non_blocking=True)
+        neat.neat_forward(rec, 100, d, x, y, launch=L, stream=stream)
+        yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        host.append((time.perf_counter() - t0) * 1e6)
+    line = {"metric": "XOR population latency (100 genomes x 4 inputs): microseconds per forward call (p50)",
+            "value": fw[0], "unit": "us", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": fw[0] / 1e3, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "XOR", "genomes": 100, "inputs_per_genome": 4},
+            "transform_us": {"p50": tr[0], "p99": tr[1]}, "forward_us": {"p50": fw[0], "p99": fw[1]},
+            "e2e": {"value": float(np.percentile(host, 50)), "unit": "us", "p99": float(np.percentile(host, 99)),
+                    "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)},
+            "clocks": clocks.summary(), "gpu_launches": 2 * reps}
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args):
@@ -698,6 +754,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "xor":
+        run_xor(args)
+        return
     if args.workload == "batched":
         run_batched(args)
         return
@@ -890,6 +949,27 @@ def main():
         except (OSError, ValueError):
             pass
 
+    # ---- fused multi-step variant, reported beside the headline (not as it):
+    # the synthetic observations do not depend on the actions, so every
+    # step's inputs are known in advance and one launch runs the episode
+    # with each genome's record held in shared memory
+    def episode_fused():
+        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        neat.neat_schedule(rec, POP, d, order, stream=stream)
+        neat.neat_forward_fused(rec, POP, d, obs, act, launch=L_batched, stream=stream)
+
+    episode_fused()
+    torch.cuda.synchronize(dev)
+    n_fused = max(1, min(args.steps, 5))
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(n_fused):
+        episode_fused()
+    f1.record(stream)
+    barrier()
+    t_fused = reduce_max(f0.elapsed_time(f1) / 1e3)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batched / args.steps * 1e3, "higher_is_better": True,
@@ -908,6 +988,10 @@ def main():
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
                 "form": f"pinned host genomes and observations in, actions out; {CH} chunks of {per} steps, "
                         "uploads and downloads overlapped with the graphs on a copy stream"},
+        "fused_multistep": {"value": world * POP * S * n_fused / t_fused, "unit": UNIT, "episodes": n_fused,
+                            "us_per_step": t_fused / n_fused / S * 1e6,
+                            "form": "one launch per episode (neat_forward_fused), records read once; valid only "
+                                    "because the synthetic observations ignore the actions, so not the headline"},
         "gpu_launches": args.steps * (2 + S),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",

@@ -256,8 +256,22 @@ NEAT_API int neat_forward_steps(const void *transformed_dev, int32_t pop, neat_d
                        const neat_launch *launch_host, neat_steps_cache **cache, void *stream);
 NEAT_API void neat_steps_cache_destroy(neat_steps_cache *cache);
 
+/* Many forwards in one launch, for input sequences known in advance (a fixed
+ * evaluation set, or observations that do not depend on the previous step's
+ * outputs): step s reads inputs_dev + s * in_step_stride ([pop][batch][I])
+ * and writes outputs_dev + s * out_step_stride ([pop][batch][O]), as
+ * neat_forward_steps, but each group keeps its genome's record in shared
+ * memory across all steps (read once per launch) and the next step's inputs
+ * are loaded during the current step.  Outputs are bit-identical to per-step
+ * forwards with the same record.  launch: NULL = neat_default_launch.
+ * Errors: NEAT_EINVAL (strides smaller than one step, launch shape),
+ * NEAT_ECUDA. */
+NEAT_API int neat_forward_fused(const void *transformed_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                int64_t in_step_stride, int32_t batch, float *outputs_dev, int64_t out_step_stride,
+                                int32_t steps, const neat_launch *launch, void *stream);
+
 /*
- * Device error word of the forward, plan, CPPN, recurrent and distance kernels: bit 0 is set when a
+ * Device error word of the forward (single-step and fused), plan, CPPN, recurrent and distance kernels: bit 0 is set when a
  * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
  * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).

@@ -150,6 +150,7 @@ _sig = {
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
     "neat_steps_cache_destroy": (None, [_P]),
+    "neat_forward_fused": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32, ctypes.POINTER(Launch), _P]),
     "neat_plan_create": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, ctypes.POINTER(PlanOptions), _P,
                                         ctypes.POINTER(_P)]),
     "neat_plan_forward": (ctypes.c_int, [_P, _i32, _P]),
@@ -452,6 +453,20 @@ class StepsCache:
             self.close()
         except Exception:
             pass
+
+
+def neat_forward_fused(transformed, pop: int, d: Dims, inputs, outputs, launch: Launch | None = None,
+                       stream=None):
+    """``steps`` forwards in one launch, the records held in shared memory
+    across steps: inputs f32 [S][P][B][I] known in advance -> outputs
+    f32 [S][P][B][O]."""
+    steps, P, B = inputs.shape[0], inputs.shape[1], inputs.shape[2]
+    assert P == pop and outputs.shape[:3] == (steps, pop, B)
+    assert inputs.is_contiguous() and outputs.is_contiguous()
+    _check(_lib.neat_forward_fused(_ptr(transformed), pop, d, _ptr(inputs), P * B * d.num_inputs, B, _ptr(outputs),
+                                   P * B * d.num_outputs, steps, ctypes.byref(launch) if launch is not None else None,
+                                   _stream(stream)), "neat_forward_fused")
+    return outputs
 
 
 def neat_forward_steps(transformed, pop: int, d: Dims, inputs, outputs, cache: StepsCache,
