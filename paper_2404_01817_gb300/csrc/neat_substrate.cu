@@ -160,7 +160,7 @@ extern "C" int neat_substrate_forward(const float *weights_dev, int32_t pop, nea
         return invalid("neat_substrate_forward: activation ids are 0..6");
     if (pop == 0 || batch == 0) return NEAT_OK;
     if (!weights_dev || !inputs_dev || !outputs_dev) return invalid("neat_substrate_forward: null pointer");
-    if (pop > 0x7fffffff / 1 || (batch + 15) / 16 > 65535) return invalid("neat_substrate_forward: too many work items");
+    if ((batch + 15) / 16 > 65535) return invalid("neat_substrate_forward: batch too large");
     SubArgs a;
     a.w = weights_dev;
     a.x = inputs_dev;
