@@ -17,6 +17,7 @@
 // the 4-byte output per query.
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 #include "neat_item.cuh"
 
 namespace neat {
@@ -141,6 +142,7 @@ using namespace neat;
 extern "C" int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_dims d, neat_substrate sub,
                                float threshold, float *weights_dev, void *stream)
 {
+    TraceRange trace_range("neat_cppn_query");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_cppn_query: invalid dims");
     if (d.num_inputs != 5 || d.num_outputs != 1)

@@ -32,6 +32,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 
 namespace neat {
 namespace {
@@ -501,6 +502,7 @@ extern "C" size_t neat_gene_stride(neat_dims d)
 extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
                                      void *genes_dev, size_t genes_bytes, uint32_t *status_dev, void *stream)
 {
+    TraceRange trace_range("neat_distance_prepare");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_distance_prepare: invalid dims");
     if (pop < 0) return invalid("neat_distance_prepare: pop < 0");
@@ -532,6 +534,7 @@ extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_
 extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *genes_b, int32_t pop_b, neat_dims d,
                              float c_disjoint, float c_homologous, float *out_dev, int64_t ld_out, void *stream)
 {
+    TraceRange trace_range("neat_distance");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_distance: invalid dims");
     if (pop_a < 0 || pop_b < 0) return invalid("neat_distance: populations must be >= 0");
@@ -592,6 +595,7 @@ extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *gen
 extern "C" int neat_speciate(const float *distances_dev, int32_t pop, int32_t n_reps, int64_t ld, float threshold,
                              int32_t *species_dev, void *stream)
 {
+    TraceRange trace_range("neat_speciate");
     clear_error();
     if (pop < 0 || n_reps < 0) return invalid("neat_speciate: sizes must be >= 0");
     if (pop == 0) return NEAT_OK;

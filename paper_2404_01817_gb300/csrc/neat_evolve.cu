@@ -20,6 +20,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 
 namespace neat {
 namespace {
@@ -445,6 +446,7 @@ extern "C" int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat
                            const uint32_t *words_dev, const float *normals_dev, const int32_t *new_keys_dev,
                            void *stream)
 {
+    TraceRange trace_range("neat_mutate");
     clear_error();
     if (!dims_ok(d) || !m) return invalid("neat_mutate: invalid dims or config");
     if (pop < 0) return invalid("neat_mutate: pop < 0");
@@ -512,6 +514,7 @@ extern "C" int neat_crossover(const float *nodes_dev, const float *conns_dev, in
                               const int32_t *parents_dev, int32_t n_children, const uint32_t *words_dev,
                               float *nodes_out_dev, float *conns_out_dev, void *stream)
 {
+    TraceRange trace_range("neat_crossover");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_crossover: invalid dims");
     if (pop < 0 || n_children < 0) return invalid("neat_crossover: sizes must be >= 0");

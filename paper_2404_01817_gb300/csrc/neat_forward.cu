@@ -19,6 +19,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 #include "neat_item.cuh"
 
 namespace neat {
@@ -384,6 +385,7 @@ extern "C" int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat
 extern "C" int neat_forward_ex(const void *transformed_dev, int32_t pop, neat_dims d, const float *inputs_dev,
                                int32_t batch, float *outputs_dev, const neat_launch *launch_host, void *stream)
 {
+    TraceRange trace_range("neat_forward");
     clear_error();
     neat_launch L;
     if (launch_host) L = *launch_host;
@@ -435,6 +437,7 @@ extern "C" int neat_forward_steps(const void *transformed_dev, int32_t pop, neat
                                   int64_t out_step_stride, int32_t steps, const neat_launch *launch_host,
                                   neat_steps_cache **cache, void *stream)
 {
+    TraceRange trace_range("neat_forward_steps");
     clear_error();
     if (!cache) return invalid("neat_forward_steps: null cache pointer");
     if (steps < 0) return invalid("neat_forward_steps: steps < 0");
@@ -570,6 +573,7 @@ __global__ void __launch_bounds__(1024) schedule_kernel(const uint8_t *rec, size
 
 extern "C" int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims d, int32_t *order_dev, void *stream)
 {
+    TraceRange trace_range("neat_schedule");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_schedule: invalid dims");
     if (pop < 0) return invalid("neat_schedule: pop < 0");

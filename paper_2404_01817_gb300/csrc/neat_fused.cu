@@ -12,6 +12,7 @@
 // the current step's level walk, so their memory latency overlaps the walk.
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 #include "neat_item.cuh"
 
 namespace neat {
@@ -164,6 +165,7 @@ extern "C" int neat_forward_fused(const void *transformed_dev, int32_t pop, neat
                                   int64_t in_step_stride, int32_t batch, float *outputs_dev, int64_t out_step_stride,
                                   int32_t steps, const neat_launch *launch_host, void *stream)
 {
+    TraceRange trace_range("neat_forward_fused");
     clear_error();
     if (steps < 0) return invalid("neat_forward_fused: steps < 0");
     if (steps == 0) return NEAT_OK;

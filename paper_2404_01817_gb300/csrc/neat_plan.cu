@@ -23,6 +23,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 #include "neat_item.cuh"
 
 namespace neat {
@@ -469,6 +470,7 @@ int autotune(neat_plan *P, cudaStream_t s)
 extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const neat_plan_options *opt,
                                 void *stream, neat_plan **out)
 {
+    TraceRange trace_range("neat_plan_create");
     clear_error();
     if (!out) return invalid("neat_plan_create: null output pointer");
     *out = nullptr;
@@ -585,6 +587,7 @@ extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const 
 
 extern "C" int neat_plan_forward(neat_plan *P, int32_t step, void *stream)
 {
+    TraceRange trace_range("neat_plan_forward");
     clear_error();
     if (!P) return invalid("neat_plan_forward: null plan");
     if (step < 0) return invalid("neat_plan_forward: step < 0");
@@ -597,6 +600,7 @@ extern "C" int neat_plan_forward(neat_plan *P, int32_t step, void *stream)
 
 extern "C" int neat_plan_forward_steps(neat_plan *P, int32_t first_step, int32_t steps, void *stream)
 {
+    TraceRange trace_range("neat_plan_forward_steps");
     clear_error();
     if (!P) return invalid("neat_plan_forward_steps: null plan");
     if (first_step < 0 || steps < 0) return invalid("neat_plan_forward_steps: negative step");
@@ -750,6 +754,7 @@ int noalloc_setup(cudaStream_t s, unsigned char **base)
 
 extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npops, int32_t step, void *stream)
 {
+    TraceRange trace_range("neat_forward_multi_noalloc");
     clear_error();
     if (!pops) return invalid("neat_forward_multi_noalloc: null populations");
     if (npops < 1 || npops > kNoallocMaxPops)

@@ -18,6 +18,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 #include "neat_item.cuh"
 
 namespace neat {
@@ -197,6 +198,7 @@ extern "C" int neat_forward_recurrent_ex(const void *transformed_dev, int32_t po
                                          const float *inputs_dev, int32_t batch, int32_t iterations,
                                          float *outputs_dev, const neat_launch *launch_host, void *stream)
 {
+    TraceRange trace_range("neat_forward_recurrent");
     clear_error();
     if (iterations < 0) return invalid("neat_forward_recurrent: iterations < 0");
     neat_launch L;

@@ -34,6 +34,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 
 namespace neat {
 namespace {
@@ -372,6 +373,7 @@ void worker_main(neat_server *S)
             }
         }
         if (!active.empty()) {
+            TraceRange trace_range("neat_serve_tick");
             const long tick = S->next_tick++;
             std::vector<GenDesc> gen;
             std::vector<BucketDev> table;

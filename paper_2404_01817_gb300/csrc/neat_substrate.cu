@@ -20,6 +20,7 @@
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 
 namespace neat {
 namespace {
@@ -152,6 +153,7 @@ extern "C" int neat_substrate_forward(const float *weights_dev, int32_t pop, nea
                                       int32_t batch, int32_t hidden_act, int32_t output_act, float *outputs_dev,
                                       void *stream)
 {
+    TraceRange trace_range("neat_substrate_forward");
     clear_error();
     if (sub.resolution < 2 || sub.resolution > 181 || sub.layers < 2)
         return invalid("neat_substrate_forward: substrate resolution must be in 2..181 and layers >= 2");

@@ -16,6 +16,7 @@
 //      position, connection row), which fixes each node's summation order.
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_trace.h"
 
 namespace neat {
 namespace {
@@ -294,6 +295,7 @@ static int transform_impl(const float *nodes_dev, const float *conns_dev, int32_
                           void *transformed_dev, size_t transformed_bytes, uint32_t *status_dev, void *stream,
                           int recurrent)
 {
+    TraceRange trace_range(recurrent ? "neat_transform_recurrent" : "neat_transform");
     clear_error();
     if (!dims_ok(d)) return invalid("neat_transform: invalid dims");
     if (pop < 0) return invalid("neat_transform: pop < 0");
