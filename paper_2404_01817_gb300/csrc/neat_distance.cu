@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
     unsigned long long *ck = nk + a.Np2;                                     // (in << 24 | out) << 13 | row
     __shared__ unsigned int st;
     __shared__ int n_nodes, n_conns;
-    const int g = blockIdx.x, tid = threadIdx.x;
+    const int g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const float *nd = a.nodes + (size_t)g * a.N * 5;
     const float4 *cn = reinterpret_cast<const float4 *>(a.conns + (size_t)g * a.C * 4);
     if (tid == 0) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
     }
     __syncthreads();
     unsigned int lst = 0;
-    for (int r = tid; r < a.Np2; r += kPrepThreads) {
+    for (int r = tid; r < a.Np2; r += nt) {
         unsigned long long v = ~0ull;
         if (r < a.N) {
             const float k = __ldg(nd + (size_t)r * 5);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
         }
         nk[r] = v;
     }
-    for (int c = tid; c < a.Cp2; c += kPrepThreads) {
+    for (int c = tid; c < a.Cp2; c += nt) {
         unsigned long long v = ~0ull;
         if (c < a.C) {
             const float4 row = __ldg(cn + c);
@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
     bitonic_sort(ck, a.Cp2);
     const int n = n_nodes, m = n_conns;
     lst = 0;
-    for (int i = tid + 1; i < n; i += kPrepThreads)
+    for (int i = tid + 1; i < n; i += nt)
         if ((nk[i] >> 32) == (nk[i - 1] >> 32)) lst |= NEAT_G_DUPKEY;
-    for (int i = tid + 1; i < m; i += kPrepThreads)
+    for (int i = tid + 1; i < m; i += nt)
         if ((ck[i] >> 13) == (ck[i - 1] >> 13)) lst |= NEAT_G_DUPCONN;
     if (lst) atomicOr(&st, lst);
     __syncthreads();
@@ -146,17 +146,17 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
     const GeneLayout L = gene_layout((uint32_t)n, (uint32_t)m);
     uint32_t *okey = reinterpret_cast<uint32_t *>(rec + L.nkey);
     uint4 *oattr = reinterpret_cast<uint4 *>(rec + L.nattr);
-    for (int j = tid; j < n; j += kPrepThreads) {
+    for (int j = tid; j < n; j += nt) {
         const unsigned long long v = nk[j];
         const float *row = nd + (size_t)(v & 0xffffffffu) * 5;
         okey[j] = (uint32_t)(v >> 32);
         oattr[j] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
                               __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
     }
-    for (int j = n + tid; j < (int)((L.nattr - L.nkey) / 4); j += kPrepThreads) okey[j] = 0xffffffffu;   // pad
+    for (int j = n + tid; j < (int)((L.nattr - L.nkey) / 4); j += nt) okey[j] = 0xffffffffu;   // pad
     unsigned long long *ockey = reinterpret_cast<unsigned long long *>(rec + L.ckey);
     float2 *ocattr = reinterpret_cast<float2 *>(rec + L.cattr);
-    for (int j = tid; j < m; j += kPrepThreads) {
+    for (int j = tid; j < m; j += nt) {
         const unsigned long long v = ck[j];
         const float4 row = __ldg(cn + (v & 0x1fffu));
         ockey[j] = v >> 13;
@@ -225,8 +225,9 @@ __device__ __forceinline__ int node_lookup(const unsigned long long *tab, uint32
     uint32_t s = slot_of(key, lg);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const unsigned long long v = tab[s];
-        if (v == kEmpty) return -1;
-        if ((uint32_t)(v >> 32) == key) return (int)(uint32_t)v;
+        const uint32_t k = (uint32_t)(v >> 32);        // all ones in a free slot, never a key
+        if (k == key) return (int)(uint32_t)v;
+        if (k == 0xffffffffu) return -1;
         s = (s + 1u) & mask;
     }
     return -1;
@@ -252,14 +253,13 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-template <bool HASH>
+template <bool HASH, int TILE>
 __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar_mem;
     __shared__ int failed;
-    __shared__ uint32_t s_n[kMaxTile], s_m[kMaxTile], s_st[kMaxTile], s_nattr[kMaxTile], s_ckey[kMaxTile],
-        s_cattr[kMaxTile];
+    __shared__ uint32_t s_n[TILE], s_m[TILE], s_st[TILE], s_nattr[TILE], s_ckey[TILE], s_cattr[TILE];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b0 = blockIdx.y * p.tile;
     const int nb = min(p.tile, p.pb - b0);
@@ -336,10 +336,10 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         {
             // node genes: each of a's genes is loaded once and looked up in
             // every staged representative (independent lookups in flight)
-            int hn[kMaxTile];
-            float sn[kMaxTile];
+            int hn[TILE];
+            float sn[TILE];
 #pragma unroll
-            for (int t = 0; t < kMaxTile; ++t) {
+            for (int t = 0; t < TILE; ++t) {
                 hn[t] = 0;
                 sn[t] = 0.0f;
             }
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                 const uint32_t key = __ldg(ka + j);
                 const uint4 x = __ldg(aa + j);
 #pragma unroll
-                for (int t = 0; t < kMaxTile; ++t) {
+                for (int t = 0; t < TILE; ++t) {
                     if (t < nb) {
                         const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
                         int i;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                 }
             }
 #pragma unroll
-            for (int t = 0; t < kMaxTile; ++t) {
+            for (int t = 0; t < TILE; ++t) {
                 if (t < nb) {
                     const int h = __reduce_add_sync(0xffffffffu, hn[t]);
                     const float v = warp_sum(sn[t]);
@@ -382,10 +382,10 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         }
         {
             // connection genes, the same way
-            int hc[kMaxTile];
-            float sc[kMaxTile];
+            int hc[TILE];
+            float sc[TILE];
 #pragma unroll
-            for (int t = 0; t < kMaxTile; ++t) {
+            for (int t = 0; t < TILE; ++t) {
                 hc[t] = 0;
                 sc[t] = 0.0f;
             }
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                 const unsigned long long key = __ldg(ka + j);
                 const float2 x = __ldg(aa + j);
 #pragma unroll
-                for (int t = 0; t < kMaxTile; ++t) {
+                for (int t = 0; t < TILE; ++t) {
                     if (t < nb) {
                         const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
                         int i;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                 }
             }
 #pragma unroll
-            for (int t = 0; t < kMaxTile; ++t) {
+            for (int t = 0; t < TILE; ++t) {
                 if (t < nb) {
                     const int h = __reduce_add_sync(0xffffffffu, hc[t]);
                     const float v = warp_sum(sc[t]);
@@ -525,7 +525,8 @@ extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(prepare_kernel), smem,
                                 "neat_distance_prepare: shared memory per block");
     if (rc) return rc;
-    prepare_kernel<<<pop, kPrepThreads, smem, as_stream(stream)>>>(a);
+    const int threads = (a.N <= 64 && a.C <= 512) ? 128 : kPrepThreads;   // small genomes: more blocks per SM
+    prepare_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_distance_prepare: launch");
     return NEAT_OK;
@@ -583,7 +584,13 @@ extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *gen
     apb = std::max<long>(kDistWarps, (apb + kDistWarps - 1) / kDistWarps * kDistWarps);
     p.a_per_block = (int)std::min<long>(apb, 1L << 30);
     const long gx = (pop_a + p.a_per_block - 1) / p.a_per_block;
-    auto kern = hash ? distance_kernel<true> : distance_kernel<false>;
+    using Kern = void (*)(DistArgs);
+    Kern kern;
+    if (p.tile > 8) kern = hash ? distance_kernel<true, 16> : distance_kernel<false, 16>;
+    else if (p.tile > 4) kern = hash ? distance_kernel<true, 8> : distance_kernel<false, 8>;
+    else if (p.tile > 2) kern = hash ? distance_kernel<true, 4> : distance_kernel<false, 4>;
+    else if (p.tile > 1) kern = hash ? distance_kernel<true, 2> : distance_kernel<false, 2>;
+    else kern = hash ? distance_kernel<true, 1> : distance_kernel<false, 1>;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_distance: shared memory per block");
     if (rc) return rc;
     kern<<<dim3((unsigned)gx, (unsigned)tiles), kDistThreads, smem, as_stream(stream)>>>(p);
