@@ -63,19 +63,22 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
 // Uniform in (0, 1) from the top 24 bits.
 __device__ __forceinline__ float unit_open(uint32_t b) { return ((float)(b >> 8) + 0.5f) * (1.0f / 16777216.0f); }
 
-// Element e of (seed, step): a standard normal by Box-Muller on one Philox
-// block per 4 elements (counter = (e / 4 low, e / 4 high, step, 0x4f4253)).
-__device__ __forceinline__ float normal_at(uint64_t seed, int step, uint64_t e)
+// Elements 4b .. 4b+3 of (seed, step): standard normals by Box-Muller on
+// Philox block b (counter = (b low, b high, step, 0x4f4253)): words (x, y)
+// give elements 4b (cos) and 4b+1 (sin), words (z, w) elements 4b+2, 4b+3.
+__device__ __forceinline__ void normals_of_block(uint64_t seed, int step, uint64_t blk, float out[4])
 {
-    const uint64_t blk = e >> 2;
     const U4 r = philox4x32_10(U4{(uint32_t)blk, (uint32_t)(blk >> 32), (uint32_t)step, 0x4f4253u}, (uint32_t)seed,
                                (uint32_t)(seed >> 32));
-    const int k = (int)(e & 3);
-    const float u1 = unit_open(k < 2 ? r.x : r.z), u2 = unit_open(k < 2 ? r.y : r.w);
-    const float rad = sqrtf(-2.0f * logf(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return rad * ((k & 1) ? s : c);
+    const float rad0 = sqrtf(-2.0f * logf(unit_open(r.x)));
+    sincospif(2.0f * unit_open(r.y), &s, &c);
+    out[0] = rad0 * c;
+    out[1] = rad0 * s;
+    const float rad1 = sqrtf(-2.0f * logf(unit_open(r.z)));
+    sincospif(2.0f * unit_open(r.w), &s, &c);
+    out[2] = rad1 * c;
+    out[3] = rad1 * s;
 }
 
 struct GenDesc {
@@ -97,11 +100,21 @@ __global__ void gen_normals_kernel(const GenDesc *__restrict__ descs, int nd)
         if (descs[mid].block_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
     const GenDesc d = descs[lo];
-    const uint64_t base = (uint64_t)(blockIdx.x - d.block_begin) * kGenPerBlock;
-    for (int k = 0; k < 4; ++k) {
-        const uint64_t e = base + (uint64_t)k * kGenThreads + threadIdx.x;
-        if (e < d.count) d.out[e] = normal_at(d.seed, d.step, e);
-    }
+    const uint64_t e0 = (uint64_t)(blockIdx.x - d.block_begin) * kGenPerBlock + 4u * threadIdx.x;
+    if (e0 >= d.count) return;
+    float z[4];
+    normals_of_block(d.seed, d.step, e0 >> 2, z);
+    for (int k = 0; k < 4 && e0 + k < d.count; ++k) d.out[e0 + k] = z[k];
+}
+
+// One descriptor, passed by value.
+__global__ void fill_normals_kernel(float *out, uint64_t count, uint64_t seed, int step)
+{
+    const uint64_t e0 = ((uint64_t)blockIdx.x * kGenThreads + threadIdx.x) * 4u;
+    if (e0 >= count) return;
+    float z[4];
+    normals_of_block(seed, step, e0 >> 2, z);
+    for (int k = 0; k < 4 && e0 + k < count; ++k) out[e0 + k] = z[k];
 }
 
 // Raw Philox words: word e = component e mod 4 of the block for counter
@@ -631,17 +644,10 @@ extern "C" int neat_fill_normal(uint64_t seed, int32_t step, int64_t count, floa
     if (count < 0 || step < 0) return invalid("neat_fill_normal: negative size or step");
     if (count == 0) return NEAT_OK;
     if (!out_dev) return invalid("neat_fill_normal: null pointer");
-    // one descriptor, passed through a small kernel-parameter copy
-    GenDesc d{out_dev, (uint64_t)count, seed, step, 0};
-    GenDesc *dd = nullptr;
-    cudaError_t e = cudaMallocAsync(&dd, sizeof(GenDesc), as_stream(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "neat_fill_normal: descriptor");
-    e = cudaMemcpyAsync(dd, &d, sizeof(d), cudaMemcpyHostToDevice, as_stream(stream));
     const long blocks = (count + kGenPerBlock - 1) / kGenPerBlock;
-    if (e == cudaSuccess && blocks <= 0x7fffffffL)
-        gen_normals_kernel<<<(unsigned)blocks, kGenThreads, 0, as_stream(stream)>>>(dd, 1);
-    cudaFreeAsync(dd, as_stream(stream));
-    e = cudaGetLastError();
+    if (blocks > 0x7fffffffL) return invalid("neat_fill_normal: count too large");
+    fill_normals_kernel<<<(unsigned)blocks, kGenThreads, 0, as_stream(stream)>>>(out_dev, (uint64_t)count, seed, step);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_fill_normal: launch");
     return NEAT_OK;
 }
