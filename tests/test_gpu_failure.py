@@ -1,7 +1,6 @@
 """Failure detection without a GPU fault: a bounded on-device wait that
 nothing satisfies gives up, reports through the device error word, and the
 context keeps working."""
-import numpy as np
 import pytest
 
 import oracle

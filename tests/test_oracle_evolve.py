@@ -9,7 +9,6 @@ split, acyclicity of feedforward connection addition, identity at rate 0,
 the exact rate and choice boundaries.
 """
 import numpy as np
-import pytest
 
 import oracle
 from paper_2404_01817_gb300 import workloads as W

@@ -8,7 +8,6 @@ device array instead.  The test calls it through the C ABI twice in a row
 the tolerance the other parity tests use.  It lives in a file of its own that
 pytest collects last, and passes alone in a fresh process or after the rest.
 """
-import ctypes
 
 import numpy as np
 import pytest
