@@ -4,16 +4,19 @@
 // expanded-connection tensor C_exp, the enabled incoming edges of every node
 // packed by destination position (layout in include/neat.h).
 //
-// All per-genome work happens in shared memory:
-//   1. node rows: presence, key and attribute checks; (key,row) pairs sorted
-//      (bitonic) so keys resolve to rows by binary search;
-//   2. connection rows: checks, endpoint lookup, duplicate (in,out) detection
-//      by sorting the key pairs;
+// All per-genome work happens in shared memory, in time linear in the rows:
+//   1. node rows: presence, key and attribute checks; keys go into an
+//      open-addressing table key -> lowest row (a duplicated key shows up on
+//      insertion);
+//   2. connection rows: checks, endpoint lookup, duplicate (in,out) pairs
+//      found by inserting them into a hash set;
 //   3. layered Kahn: one pass over the active edges per level, removing the
 //      edges of level L with shared-memory atomics; a node whose count hits
 //      zero joins level L+1;
-//   4. positions = rank of (level, row); edges sorted by (destination
-//      position, connection row), which fixes each node's summation order.
+//   4. positions = rank of (level, row), and edges in (destination position,
+//      connection row) order, each by a stable counting sort that one warp
+//      runs over the rows in chunks of 32 (ranks inside a chunk from
+//      __match_any_sync), which fixes each node's summation order.
 #include "neat_device.cuh"
 #include "neat_internal.h"
 #include "neat_trace.h"
@@ -37,21 +40,104 @@ __device__ __forceinline__ bool is_enum(float v, int n)
     return !isnan(v) && floorf(v) == v && v >= 0.0f && v < (float)n;
 }
 
-// Lowest row holding `key` among the n sorted (key << 32 | row) pairs, or -1.
-__device__ int lookup_row(const unsigned long long *map, int n, uint32_t key)
+constexpr unsigned long long kFree = ~0ull;
+
+// Open-addressing tables in shared memory: capacity a power of two at least
+// twice the number of entries, so every probe sequence reaches a free slot.
+__device__ __forceinline__ uint32_t tslot(unsigned long long x, uint32_t mask)
 {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((uint32_t)(map[mid] >> 32) < key) lo = mid + 1; else hi = mid;
+    uint32_t h = (uint32_t)x * 0x9E3779B1u ^ (uint32_t)(x >> 32) * 0x85EBCA6Bu;
+    h ^= h >> 15;
+    return h & mask;
+}
+
+// Key -> lowest row holding it (entries key << 32 | row).  True when the key
+// was already present: a duplicated key.
+__device__ bool key_insert(unsigned long long *tab, uint32_t mask, uint32_t key, uint32_t row)
+{
+    const unsigned long long v = ((unsigned long long)key << 32) | row;
+    uint32_t s = tslot(key, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long old = atomicCAS(tab + s, kFree, v);
+        if (old == kFree) return false;
+        if ((uint32_t)(old >> 32) == key) {
+            atomicMin(tab + s, v);
+            return true;
+        }
+        s = (s + 1u) & mask;
     }
-    return (lo < n && (uint32_t)(map[lo] >> 32) == key) ? (int)(map[lo] & 0xffffffffu) : -1;
+    return false;
+}
+
+// Lowest row holding `key`, or -1 (after every insertion).
+__device__ int key_row(const unsigned long long *tab, uint32_t mask, uint32_t key)
+{
+    uint32_t s = tslot(key, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long v = tab[s];
+        if (v == kFree) return -1;
+        if ((uint32_t)(v >> 32) == key) return (int)(uint32_t)v;
+        s = (s + 1u) & mask;
+    }
+    return -1;
+}
+
+// Set of (in << 24 | out) pairs.  True when the pair was already present.
+__device__ bool pair_insert(unsigned long long *tab, uint32_t mask, unsigned long long pair)
+{
+    uint32_t s = tslot(pair, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long old = atomicCAS(tab + s, kFree, pair);
+        if (old == kFree) return false;
+        if (old == pair) return true;
+        s = (s + 1u) & mask;
+    }
+    return false;
+}
+
+// In-place exclusive prefix sum of a[0..n), by the 32 threads of warp 0.
+__device__ void warp_exclusive_scan(int *a, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int x = (i < n) ? a[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < n) a[i] = carry + incl - x;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+// Stable counting placement by warp 0: items 0..count-1 in index order, item
+// i in bucket bucket_of(i) (negative: skipped), placed at start[b] + the
+// number of earlier items of bucket b (run[b] counts them chunk by chunk;
+// zero on entry).  place(i, slot) records the result.
+template <typename BucketOf, typename Place>
+__device__ void stable_place(int count, const int *start, int *run, BucketOf bucket_of, Place place)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int base = 0; base < count; base += 32) {
+        const int i = base + lane;
+        const int b = (i < count) ? bucket_of(i) : -1;
+        const unsigned m = __match_any_sync(0xffffffffu, b >= 0 ? b : -1 - lane);   // skipped items stay alone
+        if (b >= 0) place(i, start[b] + run[b] + __popc(m & below));
+        __syncwarp();
+        if (b >= 0 && lane == 31 - __clz(m)) run[b] += __popc(m);              // last item of its bucket here
+        __syncwarp();
+    }
 }
 
 __host__ __device__ inline size_t transform_smem_bytes(int N, int C, int I, int O, int Np2, int Cp2)
 {
-    size_t b = 8u * (size_t)Np2 + 8u * (size_t)Cp2;          // keymap, pairkey
-    b += 4u * (size_t)(5 * N + I + O);                        // level, indeg, cnt, pos, ebeg, io_row
+    size_t b = 16u * (size_t)Np2 + 16u * (size_t)Cp2;        // key table, pair set
+    b += 4u * (size_t)(9 * N + 1 + I + O);                    // level, indeg, cnt, pos, row, ebeg, lstart, lrun, erun, io
     b += 2u * 2u * (size_t)C;                                 // src_row, dst_row
     return (b + 15u) & ~(size_t)15u;
 }
@@ -62,15 +148,20 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     const int g = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int N = a.N, C = a.C, I = a.I, O = a.O;
+    const uint32_t kmask = 2u * (uint32_t)a.Np2 - 1u, pmask = 2u * (uint32_t)a.Cp2 - 1u;
 
-    unsigned long long *keymap = reinterpret_cast<unsigned long long *>(sm);
-    unsigned long long *pairkey = keymap + a.Np2;
-    int *level = reinterpret_cast<int *>(pairkey + a.Cp2);   // -2 absent, -1 unplaced
+    unsigned long long *ktab = reinterpret_cast<unsigned long long *>(sm);
+    unsigned long long *ptab = ktab + 2 * a.Np2;
+    int *level = reinterpret_cast<int *>(ptab + 2 * a.Cp2);   // -2 absent, -1 unplaced
     int *indeg = level + N;
     int *cnt = indeg + N;
     int *pos_of_row = cnt + N;
-    int *ebeg = pos_of_row + N;
-    int *io_row = ebeg + N;
+    int *row_of_pos = pos_of_row + N;
+    int *ebeg = row_of_pos + N;
+    int *lstart = ebeg + N;                                    // [N + 1]
+    int *lrun = lstart + N + 1;
+    int *erun = lrun + N;
+    int *io_row = erun + N;
     short *src_row = reinterpret_cast<short *>(io_row + I + O);
     short *dst_row = src_row + C;
 
@@ -83,14 +174,21 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         n_present = 0;
         n_edges = 0;
         max_level = -1;
+        lstart[N] = 0;
     }
     const float *nd = a.nodes + (size_t)g * N * 5;
     const float4 *cn = reinterpret_cast<const float4 *>(a.conns + (size_t)g * C * 4);
-    for (int r = tid; r < a.Np2; r += nt) keymap[r] = ~0ull;
-    for (int c = tid; c < a.Cp2; c += nt) pairkey[c] = ~0ull;
+    for (int i = tid; i < 2 * a.Np2; i += nt) ktab[i] = kFree;
+    for (int i = tid; i < 2 * a.Cp2; i += nt) ptab[i] = kFree;
+    for (int r = tid; r < N; r += nt) {
+        lstart[r] = 0;
+        lrun[r] = 0;
+        erun[r] = 0;
+    }
     __syncthreads();
 
-    // 1. node rows (Section 3.1 encoding; an absent row is NaN)
+    // 1. node rows (Section 3.1 encoding; an absent row is NaN); keys into
+    //    the key -> lowest row table, duplicates found on insertion
     unsigned int lst = 0;
     for (int r = tid; r < N; r += nt) {
         const float k = __ldg(nd + r * 5);
@@ -107,19 +205,16 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         }
         if (isnan(bias) || isnan(resp)) lst |= NEAT_G_BADATTR;
         level[r] = -1;
-        keymap[r] = ((unsigned long long)(uint32_t)k << 32) | (unsigned)r;
+        if (key_insert(ktab, kmask, (uint32_t)k, (uint32_t)r)) lst |= NEAT_G_DUPKEY;
         atomicAdd(&n_present, 1);
     }
     if (lst) atomicOr(&st, lst);
     __syncthreads();
-    bitonic_sort(keymap, a.Np2);
     const int n = n_present;
 
     lst = 0;
-    for (int i = tid + 1; i < n; i += nt)
-        if ((keymap[i] >> 32) == (keymap[i - 1] >> 32)) lst |= NEAT_G_DUPKEY;
     for (int j = tid; j < I + O; j += nt) {
-        const int r = lookup_row(keymap, n, (uint32_t)j);
+        const int r = key_row(ktab, kmask, (uint32_t)j);
         io_row[j] = r;
         if (r < 0) lst |= NEAT_G_MISSING_IO;
     }
@@ -131,10 +226,10 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         if (isnan(row.x) || isnan(row.y) || isnan(row.z)) continue;
         if (!is_key(row.x) || !is_key(row.y)) { lst |= NEAT_G_BADKEY; continue; }
         const uint32_t ki = (uint32_t)row.x, ko = (uint32_t)row.y;
-        pairkey[c] = ((unsigned long long)ki << 24) | ko;
+        if (pair_insert(ptab, pmask, ((unsigned long long)ki << 24) | ko)) lst |= NEAT_G_DUPCONN;
         if (row.z == 0.0f) continue;
         if (isnan(row.w)) lst |= NEAT_G_BADATTR;
-        const int s = lookup_row(keymap, n, ki), d = lookup_row(keymap, n, ko);
+        const int s = key_row(ktab, kmask, ki), d = key_row(ktab, kmask, ko);
         if (s < 0 || d < 0) { lst |= NEAT_W_DANGLING; continue; }
         if (ko < (uint32_t)I) { lst |= NEAT_W_INTO_INPUT; continue; }
         src_row[c] = (short)s;
@@ -144,17 +239,12 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     }
     if (lst) atomicOr(&st, lst);
     __syncthreads();
-    bitonic_sort(pairkey, a.Cp2);
 
-    lst = 0;
-    for (int i = tid + 1; i < a.Cp2; i += nt)
-        if (pairkey[i] != ~0ull && pairkey[i] == pairkey[i - 1]) lst |= NEAT_G_DUPCONN;
     // 3. layered Kahn: level 0 = present nodes without enabled incoming edges
     for (int r = tid; r < N; r += nt) {
         cnt[r] = indeg[r];
         if (level[r] == -1 && (indeg[r] == 0 || a.recurrent)) level[r] = 0;
     }
-    if (lst) atomicOr(&st, lst);
     for (int L = 0; !a.recurrent; ++L) {
         if (tid == 0) changed = 0;
         __syncthreads();
@@ -194,51 +284,50 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         return;
     }
 
-    // 4. positions: rank of (level, row)
+    // 4. positions = rank of (level, row): a stable counting sort by level
     const int nl = max_level + 1;
     const int E = n_edges;
     const uint32_t off_edge = kHeaderBytes + kNodeBytes * (uint32_t)n;
     const uint32_t off_level = align16(off_edge + kEdgeBytes * (uint32_t)E);
     const uint32_t off_io = align16(off_level + 2u * (uint32_t)(nl + 1));
     const uint32_t used = align16(off_io + 2u * (uint32_t)(I + O));
-
-    uint32_t *ordkey = reinterpret_cast<uint32_t *>(keymap);
-    for (int r = tid; r < a.Np2; r += nt)
-        ordkey[r] = (r < N && level[r] >= 0) ? (((uint32_t)level[r] << 11) | (uint32_t)r) : 0xffffffffu;
+    for (int r = tid; r < N; r += nt)
+        if (level[r] >= 0) atomicAdd(&lstart[level[r]], 1);
     __syncthreads();
-    bitonic_sort(ordkey, a.Np2);
-    uint16_t *lev_out = reinterpret_cast<uint16_t *>(rec + off_level);
-    for (int p = tid; p < n; p += nt) {
-        const uint32_t key = ordkey[p];
-        pos_of_row[key & 0x7ffu] = p;
-        if (p == 0 || (ordkey[p - 1] >> 11) != (key >> 11)) lev_out[key >> 11] = (uint16_t)p;
+    if (tid < 32) {
+        warp_exclusive_scan(lstart, nl);
+        __syncwarp();
+        stable_place(N, lstart, lrun, [&](int r) { return level[r]; },
+                     [&](int r, int p) {
+                         pos_of_row[r] = p;
+                         row_of_pos[p] = r;
+                     });
     }
+    __syncthreads();
+    uint16_t *lev_out = reinterpret_cast<uint16_t *>(rec + off_level);
+    for (int L = tid; L < nl; L += nt) lev_out[L] = (uint16_t)lstart[L];
     if (tid == 0) lev_out[nl] = (uint16_t)n;
-    uint32_t *edgekey = reinterpret_cast<uint32_t *>(pairkey);
-    __syncthreads();
-    for (int c = tid; c < a.Cp2; c += nt)
-        edgekey[c] = (c < C && dst_row[c] >= 0)
-                         ? (((uint32_t)pos_of_row[dst_row[c]] << 13) | (uint32_t)c) : 0xffffffffu;
-    for (int p = tid; p < N; p += nt) ebeg[p] = 0;
-    __syncthreads();
-    bitonic_sort(edgekey, a.Cp2);
 
-    // 5. edges in (destination position, connection row) order
+    // 5. edges in (destination position, connection row) order: a stable
+    //    counting sort by destination position
+    for (int p = tid; p < n; p += nt) ebeg[p] = cnt[row_of_pos[p]];
+    __syncthreads();
     uint2 *edges = reinterpret_cast<uint2 *>(rec + off_edge);
-    for (int k = tid; k < E; k += nt) {
-        const uint32_t key = edgekey[k];
-        const int c = (int)(key & 0x1fffu);
-        const int dp = (int)(key >> 13);
-        if (k == 0 || (edgekey[k - 1] >> 13) != (uint32_t)dp) ebeg[dp] = k;
-        const float w = __ldg(a.conns + ((size_t)g * C + c) * 4 + 3);
-        edges[k] = make_uint2(__float_as_uint(w), (uint32_t)pos_of_row[src_row[c]]);
+    if (tid < 32) {
+        warp_exclusive_scan(ebeg, n);
+        __syncwarp();
+        stable_place(C, ebeg, erun, [&](int c) { return dst_row[c] >= 0 ? pos_of_row[dst_row[c]] : -1; },
+                     [&](int c, int k) {
+                         const float w = __ldg(a.conns + ((size_t)g * C + c) * 4 + 3);
+                         edges[k] = make_uint2(__float_as_uint(w), (uint32_t)pos_of_row[src_row[c]]);
+                     });
     }
     __syncthreads();
 
     // 6. node entries by position, io positions, header
     uint4 *nodes_out = reinterpret_cast<uint4 *>(rec + kHeaderBytes);
     for (int p = tid; p < n; p += nt) {
-        const int r = (int)(ordkey[p] & 0x7ffu);
+        const int r = row_of_pos[p];
         const float key = __ldg(nd + r * 5);
         const float bias = __ldg(nd + r * 5 + 1), resp = __ldg(nd + r * 5 + 2);
         const uint32_t agg = (uint32_t)__ldg(nd + r * 5 + 3);
@@ -252,7 +341,7 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     if (tid == 0) lead_inputs = n;
     __syncthreads();
     for (int p = tid; p < n; p += nt)
-        if (__ldg(nd + (ordkey[p] & 0x7ffu) * 5) >= (float)I) atomicMin(&lead_inputs, p);
+        if (__ldg(nd + row_of_pos[p] * 5) >= (float)I) atomicMin(&lead_inputs, p);
     __syncthreads();
     uint16_t *io_out = reinterpret_cast<uint16_t *>(rec + off_io);
     for (int j = tid; j < I + O; j += nt) io_out[j] = (uint16_t)pos_of_row[io_row[j]];
