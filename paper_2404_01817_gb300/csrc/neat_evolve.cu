@@ -14,12 +14,13 @@
 // searches, and for feedforward networks a breadth-first reachability sweep
 // over the connections); the attribute step then updates every present row
 // in parallel.  Crossover: one block per child, the second parent's node
-// keys and (in, out) pairs sorted in shared memory (bitonic) and looked up by
-// binary search for every row of the first parent.
+// keys and (in, out) pairs in shared-memory hash tables (lowest row per key
+// or pair) looked up for every row of the first parent.
 #include <algorithm>
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_hash.cuh"
 #include "neat_trace.h"
 
 namespace neat {
@@ -330,9 +331,9 @@ struct CrossArgs {
 __global__ void __launch_bounds__(kEvoThreads) crossover_kernel(const CrossArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    unsigned long long *nmap = reinterpret_cast<unsigned long long *>(sm);   // key << 32 | row
-    unsigned long long *cmap = nmap + a.Np2;                                  // (in << 24 | out) << 13 | row
-    __shared__ int s_n, s_m;
+    unsigned long long *ntab = reinterpret_cast<unsigned long long *>(sm);   // key -> lowest row of p2
+    unsigned long long *ctab = ntab + 2 * a.Np2;                              // (in, out) -> lowest row of p2
+    const uint32_t nmask = 2u * (uint32_t)a.Np2 - 1u, cmask = 2u * (uint32_t)a.Cp2 - 1u;
     const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int N = a.N, C = a.C;
     const int p1 = __ldg(a.parents + 2 * k), p2 = __ldg(a.parents + 2 * k + 1);
@@ -341,54 +342,28 @@ __global__ void __launch_bounds__(kEvoThreads) crossover_kernel(const CrossArgs 
     float *no = a.nodes_out + (size_t)k * N * 5;
     float *co = a.conns_out + (size_t)k * C * 4;
     const uint32_t *w = a.words + (size_t)k * (N + C);
-    if (tid == 0) {
-        s_n = 0;
-        s_m = 0;
+    for (int i = tid; i < 2 * a.Np2; i += nt) ntab[i] = kFree;
+    for (int i = tid; i < 2 * a.Cp2; i += nt) ctab[i] = kFree;
+    __syncthreads();
+    for (int r = tid; r < N; r += nt) {
+        const float key = __ldg(n2 + (size_t)r * 5);
+        if (is_key(key)) key_insert(ntab, nmask, (uint32_t)key, (uint32_t)r);
+    }
+    for (int c = tid; c < C; c += nt) {
+        const float4 y = __ldg(reinterpret_cast<const float4 *>(c2) + c);
+        if (is_key(y.x) && is_key(y.y) && !isnan(y.z))
+            pair_row_insert(ctab, cmask, ((unsigned long long)(uint32_t)y.x << 24) | (uint32_t)y.y, (uint32_t)c);
     }
     __syncthreads();
-    int cn = 0, cm = 0;
-    for (int r = tid; r < a.Np2; r += nt) {
-        unsigned long long v = ~0ull;
-        if (r < N) {
-            const float key = __ldg(n2 + (size_t)r * 5);
-            if (is_key(key)) {
-                v = ((unsigned long long)(uint32_t)key << 32) | (unsigned)r;
-                ++cn;
-            }
-        }
-        nmap[r] = v;
-    }
-    for (int c = tid; c < a.Cp2; c += nt) {
-        unsigned long long v = ~0ull;
-        if (c < C) {
-            const float4 y = __ldg(reinterpret_cast<const float4 *>(c2) + c);
-            if (is_key(y.x) && is_key(y.y) && !isnan(y.z)) {
-                v = ((((unsigned long long)(uint32_t)y.x << 24) | (uint32_t)y.y) << 13) | (unsigned)c;
-                ++cm;
-            }
-        }
-        cmap[c] = v;
-    }
-    atomicAdd(&s_n, cn);
-    atomicAdd(&s_m, cm);
-    __syncthreads();
-    bitonic_sort(nmap, a.Np2);
-    bitonic_sort(cmap, a.Cp2);
-    const int n_map = s_n, m_map = s_m;
     for (int r = tid; r < N; r += nt) {
         const float *x = n1 + (size_t)r * 5;
         float v[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] = __ldg(x + j);
         if (is_key(v[0]) && w[r] >= 0x80000000u) {
-            const uint32_t key = (uint32_t)v[0];
-            int lo = 0, hi = n_map;                          // lowest row of p2 holding the key
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((uint32_t)(nmap[mid] >> 32) < key) lo = mid + 1; else hi = mid;
-            }
-            if (lo < n_map && (uint32_t)(nmap[lo] >> 32) == key) {
-                const float *y = n2 + (size_t)(uint32_t)nmap[lo] * 5;
+            const int q = key_row(ntab, nmask, (uint32_t)v[0]);     // p2's lowest row with the key
+            if (q >= 0) {
+                const float *y = n2 + (size_t)q * 5;
 #pragma unroll
                 for (int j = 1; j < 5; ++j) v[j] = __ldg(y + j);
             }
@@ -399,14 +374,9 @@ __global__ void __launch_bounds__(kEvoThreads) crossover_kernel(const CrossArgs 
     for (int c = tid; c < C; c += nt) {
         float4 x = __ldg(reinterpret_cast<const float4 *>(c1) + c);
         if (is_key(x.x) && is_key(x.y) && !isnan(x.z) && w[N + c] >= 0x80000000u) {
-            const unsigned long long pair = ((unsigned long long)(uint32_t)x.x << 24) | (uint32_t)x.y;
-            int lo = 0, hi = m_map;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((cmap[mid] >> 13) < pair) lo = mid + 1; else hi = mid;
-            }
-            if (lo < m_map && (cmap[lo] >> 13) == pair) {
-                const float4 y = __ldg(reinterpret_cast<const float4 *>(c2) + (cmap[lo] & 0x1fffu));
+            const int q = pair_row(ctab, cmask, ((unsigned long long)(uint32_t)x.x << 24) | (uint32_t)x.y);
+            if (q >= 0) {
+                const float4 y = __ldg(reinterpret_cast<const float4 *>(c2) + q);
                 x.z = y.z;
                 x.w = y.w;
             }
@@ -536,7 +506,7 @@ extern "C" int neat_crossover(const float *nodes_dev, const float *conns_dev, in
     a.C = d.max_conns;
     a.Np2 = pow2_at_least(a.N);
     a.Cp2 = pow2_at_least(a.C > 0 ? a.C : 1);
-    const size_t smem = 8u * ((size_t)a.Np2 + (size_t)a.Cp2);
+    const size_t smem = 16u * ((size_t)a.Np2 + (size_t)a.Cp2);
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(crossover_kernel), smem, "neat_crossover: shared memory");
     if (rc) return rc;
     const int threads = (a.N <= 64 && a.C <= 256) ? 128 : kEvoThreads;

@@ -19,6 +19,7 @@
 //      __match_any_sync), which fixes each node's summation order.
 #include "neat_device.cuh"
 #include "neat_internal.h"
+#include "neat_hash.cuh"
 #include "neat_trace.h"
 
 namespace neat {
@@ -38,61 +39,6 @@ struct TransformArgs {
 __device__ __forceinline__ bool is_enum(float v, int n)
 {
     return !isnan(v) && floorf(v) == v && v >= 0.0f && v < (float)n;
-}
-
-constexpr unsigned long long kFree = ~0ull;
-
-// Open-addressing tables in shared memory: capacity a power of two at least
-// twice the number of entries, so every probe sequence reaches a free slot.
-__device__ __forceinline__ uint32_t tslot(unsigned long long x, uint32_t mask)
-{
-    uint32_t h = (uint32_t)x * 0x9E3779B1u ^ (uint32_t)(x >> 32) * 0x85EBCA6Bu;
-    h ^= h >> 15;
-    return h & mask;
-}
-
-// Key -> lowest row holding it (entries key << 32 | row).  True when the key
-// was already present: a duplicated key.
-__device__ bool key_insert(unsigned long long *tab, uint32_t mask, uint32_t key, uint32_t row)
-{
-    const unsigned long long v = ((unsigned long long)key << 32) | row;
-    uint32_t s = tslot(key, mask);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long old = atomicCAS(tab + s, kFree, v);
-        if (old == kFree) return false;
-        if ((uint32_t)(old >> 32) == key) {
-            atomicMin(tab + s, v);
-            return true;
-        }
-        s = (s + 1u) & mask;
-    }
-    return false;
-}
-
-// Lowest row holding `key`, or -1 (after every insertion).
-__device__ int key_row(const unsigned long long *tab, uint32_t mask, uint32_t key)
-{
-    uint32_t s = tslot(key, mask);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long v = tab[s];
-        if (v == kFree) return -1;
-        if ((uint32_t)(v >> 32) == key) return (int)(uint32_t)v;
-        s = (s + 1u) & mask;
-    }
-    return -1;
-}
-
-// Set of (in << 24 | out) pairs.  True when the pair was already present.
-__device__ bool pair_insert(unsigned long long *tab, uint32_t mask, unsigned long long pair)
-{
-    uint32_t s = tslot(pair, mask);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long old = atomicCAS(tab + s, kFree, pair);
-        if (old == kFree) return false;
-        if (old == pair) return true;
-        s = (s + 1u) & mask;
-    }
-    return false;
 }
 
 // In-place exclusive prefix sum of a[0..n), by the 32 threads of warp 0.
