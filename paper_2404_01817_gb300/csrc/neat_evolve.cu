@@ -11,8 +11,8 @@
 // tensors.  The node keys and the connections' (in, out, enabled) columns
 // are kept in shared memory while the four structural steps run one after
 // another (block-wide counts, rank selection by a block scan, first-free-row
-// searches, and for feedforward networks a breadth-first reachability sweep
-// over the connections); the attribute step then updates every present row
+// searches, and for feedforward networks a key -> row hash table and a
+// breadth-first reachability sweep over the connections); the attribute step then updates every present row
 // in parallel.  Crossover: one block per child, the second parent's node
 // keys and (in, out) pairs in shared-memory hash tables (lowest row per key
 // or pair) looked up for every row of the first parent.
@@ -97,28 +97,18 @@ __device__ int select_rank(int R, Pred pred, int rank, int *s_cnt, int *s_row, i
     return row;
 }
 
-__device__ __forceinline__ int lookup_key_row(const unsigned long long *map, int n, uint32_t key)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((uint32_t)(map[mid] >> 32) < key) lo = mid + 1; else hi = mid;
-    }
-    return (lo < n && (uint32_t)(map[lo] >> 32) == key) ? (int)(uint32_t)map[lo] : -1;
-}
-
 __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    unsigned long long *map = reinterpret_cast<unsigned long long *>(sm);   // [Np2] key << 32 | row
-    float *nk = reinterpret_cast<float *>(map + a.Np2);                      // [N] node keys
+    unsigned long long *map = reinterpret_cast<unsigned long long *>(sm);   // [2 Np2] key -> lowest row table
+    float *nk = reinterpret_cast<float *>(map + 2 * a.Np2);                  // [N] node keys
     float *ci = nk + a.N;                                                     // [C] in keys
     float *co = ci + a.C;                                                     // [C] out keys
     float *ce = co + a.C;                                                     // [C] enabled
     short *inr = reinterpret_cast<short *>(ce + a.C);                        // [C] rows of the endpoints
     short *outr = inr + a.C;
     unsigned char *seen = reinterpret_cast<unsigned char *>(outr + a.C);     // [N]
-    __shared__ int s_cnt[kEvoThreads / 32], s_row, s_n_map;
+    __shared__ int s_cnt[kEvoThreads / 32], s_row;
     const int g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int N = a.N, C = a.C;
     float *nodes = a.nodes + (size_t)g * N * 5;
@@ -222,30 +212,25 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
                     if (s == t) {
                         reject = true;
                     } else {
-                        // key -> lowest row map of the present nodes, endpoint rows
-                        // of the connections, then a sweep from t until s is seen
-                        for (int r = tid; r < a.Np2; r += nt)
-                            map[r] = (r < N && node_present(r))
-                                         ? ((unsigned long long)(uint32_t)nk[r] << 32) | (unsigned)r
-                                         : ~0ull;
-                        if (tid == 0) s_n_map = 0;
+                        // key -> lowest row table of the present nodes, endpoint
+                        // rows of the connections, then a sweep from t until s is seen
+                        const uint32_t kmask = 2u * (uint32_t)a.Np2 - 1u;
+                        for (int i = tid; i < 2 * a.Np2; i += nt) map[i] = kFree;
                         __syncthreads();
-                        int cnt = 0;
-                        for (int r = tid; r < N; r += nt) cnt += node_present(r) ? 1 : 0;
-                        atomicAdd(&s_n_map, cnt);
-                        bitonic_sort(map, a.Np2);
-                        const int nmap = s_n_map;
+                        for (int r = tid; r < N; r += nt)
+                            if (node_present(r)) key_insert(map, kmask, (uint32_t)nk[r], (uint32_t)r);
+                        __syncthreads();
                         for (int c = tid; c < C; c += nt) {
                             inr[c] = outr[c] = -1;
                             if (conn_present(c)) {
-                                inr[c] = (short)lookup_key_row(map, nmap, (uint32_t)ci[c]);
-                                outr[c] = (short)lookup_key_row(map, nmap, (uint32_t)co[c]);
+                                inr[c] = (short)key_row(map, kmask, (uint32_t)ci[c]);
+                                outr[c] = (short)key_row(map, kmask, (uint32_t)co[c]);
                             }
                         }
                         for (int r = tid; r < N; r += nt) seen[r] = 0;
                         __syncthreads();
-                        const int row_s = lookup_key_row(map, nmap, (uint32_t)s);
-                        const int row_t = lookup_key_row(map, nmap, (uint32_t)t);
+                        const int row_s = key_row(map, kmask, (uint32_t)s);
+                        const int row_t = key_row(map, kmask, (uint32_t)t);
                         if (tid == 0) seen[row_t] = 1;
                         __syncthreads();
                         for (int it = 0; it <= N; ++it) {
@@ -469,7 +454,7 @@ extern "C" int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat
     for (int i = 0; i < 8; ++i) a.act_opt[i] = m->activation_options[i];
     for (int i = 0; i < 4; ++i) a.agg_opt[i] = m->aggregation_options[i];
     a.feedforward = m->feedforward != 0;
-    const size_t smem = 8u * (size_t)a.Np2 + 4u * (size_t)a.N + 12u * (size_t)a.C + 4u * (size_t)a.C +
+    const size_t smem = 16u * (size_t)a.Np2 + 4u * (size_t)a.N + 12u * (size_t)a.C + 4u * (size_t)a.C +
                         (size_t)a.N + 16u;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(mutate_kernel), smem, "neat_mutate: shared memory");
     if (rc) return rc;
