@@ -519,7 +519,8 @@ typedef struct neat_pop_desc {
 typedef struct neat_plan_options {
     int32_t autotune;       /* 1: time candidate shapes per bucket at creation (runs kernels on the plan's buffers) */
     int32_t size_buckets;   /* 1: split populations by node count; 0: one bucket per population */
-    int32_t block_threads;  /* threads of a persistent block (0: 256) */
+    int32_t block_threads;  /* threads of a persistent block (0: with autotune, the fastest of
+                               256, 512 and 1024 on the plan's data; without, 256) */
     int32_t pdl;            /* 1: steps after the first use programmatic dependent launch */
 } neat_plan_options;
 

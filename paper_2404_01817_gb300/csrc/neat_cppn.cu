@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
         if (sum_only)
             for (int p = first; p < n_nodes; ++p) eval_node_sum<false>(nodes[p], edges, v, p, lgT, tid);
         else
-            for (int p = first; p < n_nodes; ++p) eval_node<false, false>(nodes[p], edges, v, p, lgT, tid);
+            for (int p = first; p < n_nodes; ++p) eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid);
         const float w = v[(pout << lgT) + tid];
         out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
         r += kCppnThreads;

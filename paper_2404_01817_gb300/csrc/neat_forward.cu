@@ -370,8 +370,13 @@ extern "C" int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat
         int t = 1;
         while (t < batch && t < 32) t <<= 1;
         L.tile = t;
-        const int nsub = N <= 32 ? 1 : (N <= 128 ? 2 : (N <= 512 ? 4 : 8));
-        L.group = t * nsub;
+        L.group = t * tile_row_threads(N);
+        // a group's record and value tile must fit one block's shared memory
+        const size_t rec = record_max_bytes(d.num_inputs, d.num_outputs, N, d.max_conns);
+        while (L.tile > 1 && rec + 4u * (size_t)N * L.tile > kMaxGroupSmem) {
+            L.tile >>= 1;
+            L.group >>= 1;
+        }
     }
     const size_t per_group = record_max_bytes(d.num_inputs, d.num_outputs, N, d.max_conns) +
                              4u * (size_t)((N * L.tile + 3) & ~3);

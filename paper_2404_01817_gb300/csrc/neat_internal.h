@@ -54,6 +54,20 @@ constexpr size_t kMaxSmemPerBlock = 227u * 1024u;
 int allow_dynamic_smem(const void *kernel, size_t dynamic_bytes, const char *what);
 
 // ---------------------------------------------------------- forward args
+// Shared memory one group's record and value tiles may take in a default
+// launch shape (room left for the block's barriers).
+constexpr size_t kMaxGroupSmem = 200u * 1024u;
+
+// Threads per tile row for a genome of up to n nodes and a batch of several
+// input vectors: about one per 32 nodes (a level of a large genome holds
+// tens of nodes), a power of two in 1..16.
+inline int tile_row_threads(int n)
+{
+    int nsub = 1;
+    while (nsub < 16 && nsub * 2 * 32 <= n) nsub <<= 1;
+    return nsub;
+}
+
 struct ForwardArgs {
     const uint8_t *rec;      // records, one per genome, `stride` bytes apart
     size_t stride;

@@ -109,18 +109,49 @@ __device__ __forceinline__ float node_output(const uint4 ne, uint32_t agg, uint3
     return activate(act, fmaf(__uint_as_float(ne.y), a, __uint_as_float(ne.x)));
 }
 
-// One whole node for one column (one thread): all four partials.
-template <bool T1, bool FAST>
-__device__ __forceinline__ void eval_node(const uint4 ne, const uint2 *__restrict__ edges,
-                                          float *__restrict__ v, int p, int lgT, int col)
+// The four partials of one node for one column of a tile, combined along
+// the tree, for a compile-time aggregation AGG (sum also serves mean): the
+// operations of `partials` with all four partials, in the same order, so the
+// bits are those of every other shape.  One loop per aggregation instead of
+// a select among the three per edge.
+template <uint32_t AGG>
+__device__ __forceinline__ float partials_agg(const uint2 *__restrict__ e, uint32_t ec,
+                                              const float *__restrict__ v, int lgT, int col)
+{
+    const float id = agg_identity(AGG);
+    float q0 = id, q1 = id, q2 = id, q3 = id;
+    uint32_t i = 0;
+#pragma unroll 2
+    for (; i + 4 <= ec; i += 4) {
+        const uint2 t0 = e[i], t1 = e[i + 1], t2 = e[i + 2], t3 = e[i + 3];
+        q0 = agg_step(AGG, q0, __uint_as_float(t0.x), v[vslot<false>(t0.y, lgT, col)]);
+        q1 = agg_step(AGG, q1, __uint_as_float(t1.x), v[vslot<false>(t1.y, lgT, col)]);
+        q2 = agg_step(AGG, q2, __uint_as_float(t2.x), v[vslot<false>(t2.y, lgT, col)]);
+        q3 = agg_step(AGG, q3, __uint_as_float(t3.x), v[vslot<false>(t3.y, lgT, col)]);
+    }
+    if (i < ec) { const uint2 t = e[i]; q0 = agg_step(AGG, q0, __uint_as_float(t.x), v[vslot<false>(t.y, lgT, col)]); }
+    if (i + 1 < ec) { const uint2 t = e[i + 1]; q1 = agg_step(AGG, q1, __uint_as_float(t.x), v[vslot<false>(t.y, lgT, col)]); }
+    if (i + 2 < ec) { const uint2 t = e[i + 2]; q2 = agg_step(AGG, q2, __uint_as_float(t.x), v[vslot<false>(t.y, lgT, col)]); }
+    return agg_combine(AGG, agg_combine(AGG, q0, q1), agg_combine(AGG, q2, q3));
+}
+
+// One whole node for one column of a tile (one thread), the aggregation
+// dispatched once per node: the threads of a node row take the same branch.
+template <bool FAST>
+__device__ __forceinline__ void eval_node_tile(const uint4 ne, const uint2 *__restrict__ edges,
+                                               float *__restrict__ v, int p, int lgT, int col)
 {
     const uint32_t act = ne.w & 0xffu;
     if (act == kInputAct) return;
     const uint32_t agg = FAST ? kAggSum : ((ne.w >> 8) & 0xffu);
     const uint32_t ec = ne.z >> 16;
-    const float a = partials<T1, FAST>(agg, edges + (ne.z & 0xffffu), ec, v, lgT, col, 0, 4);
-    v[vslot<T1>(p, lgT, col)] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
-                                     : node_output(ne, agg, act, ec, a);
+    const uint2 *e = edges + (ne.z & 0xffffu);
+    float a;
+    if (FAST || agg == kAggSum || agg == kAggMean) a = partials_agg<kAggSum>(e, ec, v, lgT, col);
+    else if (agg == kAggProduct) a = partials_agg<kAggProduct>(e, ec, v, lgT, col);
+    else a = partials_agg<kAggMax>(e, ec, v, lgT, col);
+    v[vslot<false>(p, lgT, col)] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
+                                        : node_output(ne, agg, act, ec, a);
 }
 
 // One whole node for one column when every non-input node of the genome
@@ -215,13 +246,13 @@ __device__ __forceinline__ void walk_levels(const uint4 *srec, float *v, int G, 
         const int nsub = G >> lgT;
         if (nsub == 1) {
             if (col_ok)
-                for (int p = 0; p < n_nodes; ++p) eval_node<false, FAST>(nodes[p], edges, v, p, lgT, col);
+                for (int p = 0; p < n_nodes; ++p) eval_node_tile<FAST>(nodes[p], edges, v, p, lgT, col);
         } else {
             int p0 = lev[0];
             for (int l = 0; l < n_levels; ++l) {
                 const int p1 = lev[l + 1];
                 if (col_ok)
-                    for (int p = p0 + sub; p < p1; p += nsub) eval_node<false, FAST>(nodes[p], edges, v, p, lgT, col);
+                    for (int p = p0 + sub; p < p1; p += nsub) eval_node_tile<FAST>(nodes[p], edges, v, p, lgT, col);
                 p0 = p1;
                 group_sync(G, gi);
             }

@@ -112,18 +112,30 @@ int lg(int x)
     return l;
 }
 
-Shape heuristic_shape(int n_class, int batch)
+// A shape the kernels can index: G and tile powers of two, tile <= G <= NT,
+// split 1, 2 or 4 (a bad shape would mis-index shared memory, so it is
+// refused on the host before any launch).
+bool shape_ok(const Shape &s, int NT)
+{
+    const auto p2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+    return p2(s.G) && s.G <= NT && p2(s.tile) && s.tile <= s.G && (s.split == 1 || s.split == 2 || s.split == 4);
+}
+
+// Launch shape without timing: as neat_default_launch, with groups of at
+// most NT threads (the persistent block).
+Shape heuristic_shape(int n_class, int batch, int NT)
 {
     Shape s;
     s.split = 1;
     if (batch <= 1) {
         s.tile = 1;
-        s.G = n_class <= 64 ? 8 : (n_class <= 256 ? 16 : 32);
+        s.G = std::min(NT, n_class <= 64 ? 8 : (n_class <= 256 ? 16 : 32));
     } else {
         int t = 1;
-        while (t < batch && t < 32) t <<= 1;
+        while (t < batch && t < 32 && t < NT) t <<= 1;
         s.tile = t;
-        const int nsub = n_class <= 32 ? 1 : (n_class <= 128 ? 2 : (n_class <= 512 ? 4 : 8));
+        int nsub = tile_row_threads(n_class);
+        while (nsub > 1 && t * nsub > NT) nsub >>= 1;
         s.G = t * nsub;
     }
     return s;
@@ -206,6 +218,7 @@ int layout(neat_plan *P, cudaStream_t s)
         d.tile = h.shape.tile;
         d.tiles = (pd.batch + d.tile - 1) / d.tile;
         d.lg_split = lg(h.shape.split);
+        if (!shape_ok(h.shape, NT)) return invalid("plan: invalid bucket launch shape");
         d.G = h.shape.G;
         d.lgG = lg(d.G);
         const size_t reg = region_bytes(h, d.I, d.O);
@@ -391,7 +404,7 @@ size_t footprint(const neat_plan *P, const HostBucket &h)
     return region_bytes(h, 0, 0) * gpc;
 }
 
-int autotune(neat_plan *P, cudaStream_t s)
+int autotune(neat_plan *P, cudaStream_t s, float *step_ms)
 {
     char line[256];
     auto position_of = [&](size_t hbi) {
@@ -459,8 +472,48 @@ int autotune(neat_plan *P, cudaStream_t s)
                  hbi ? "," : "", h.pop_index, h.n_class, h.shape.G, h.shape.tile, h.shape.split);
         P->autotune_log += line;
     }
-    snprintf(line, sizeof(line), ",{\"step_ms\":%.5f}", best_ms);
+    snprintf(line, sizeof(line), ",{\"block_threads\":%d,\"step_ms\":%.5f}", P->block_threads, best_ms);
     P->autotune_log += line;
+    if (step_ms) *step_ms = best_ms;
+    return layout(P, s);
+}
+
+// Autotune at each persistent block size and keep the fastest: large
+// groups (a tile row of many threads for genomes of hundreds of nodes) need
+// large blocks, many small groups share smaller ones well.
+int autotune_block_threads(neat_plan *P, cudaStream_t s)
+{
+    struct Best {
+        float ms = -1.0f;
+        int NT = 0;
+        std::vector<Shape> shapes;
+        std::string log;
+    } best;
+    for (int NT : {256, 512, 1024}) {
+        P->block_threads = NT;
+        P->autotune_log.clear();
+        for (HostBucket &b : P->hb) b.shape = heuristic_shape(b.n_class, P->pops[b.pop_index].batch, NT);
+        int rc = layout(P, s);
+        float ms = -1.0f;
+        if (rc == NEAT_OK) rc = autotune(P, s, &ms);
+        if (rc != NEAT_OK) {
+            cudaGetLastError();
+            clear_error();
+            continue;
+        }
+        if (best.ms < 0.0f || ms < best.ms) {
+            best.ms = ms;
+            best.NT = NT;
+            best.shapes.clear();
+            for (const HostBucket &b : P->hb) best.shapes.push_back(b.shape);
+            best.log = P->autotune_log;
+        }
+    }
+    if (best.NT == 0) return invalid("neat_plan_create: no block size could be tuned");
+    P->block_threads = best.NT;
+    P->opt.block_threads = best.NT;
+    for (size_t i = 0; i < P->hb.size(); ++i) P->hb[i].shape = best.shapes[i];
+    P->autotune_log = best.log;
     return layout(P, s);
 }
 
@@ -476,8 +529,9 @@ extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const 
     *out = nullptr;
     if (!pops || npops < 1) return invalid("neat_plan_create: no populations");
     cudaStream_t s = as_stream(stream);
-    neat_plan_options o = {0, 1, 256, 1};
+    neat_plan_options o = {0, 1, 0, 1};
     if (opt) o = *opt;
+    const bool tune_block = o.autotune && o.block_threads == 0;
     if (o.block_threads == 0) o.block_threads = 256;
     if (o.block_threads < 32 || o.block_threads > 1024 || (o.block_threads & (o.block_threads - 1)))
         return invalid("neat_plan_create: block_threads must be a power of two in 32..1024");
@@ -549,7 +603,7 @@ extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const 
             if (lx != ly) return lx > ly;
             return h[(size_t)x * 8 + 1] > h[(size_t)y * 8 + 1];
         });
-        b.shape = heuristic_shape(b.n_class, P->pops[b.pop_index].batch);
+        b.shape = heuristic_shape(b.n_class, P->pops[b.pop_index].batch, P->block_threads);
     }
     size_t total = 0;
     for (const HostBucket &b : P->hb) total += b.gidx.size();
@@ -572,7 +626,8 @@ extern "C" int neat_plan_create(const neat_pop_desc *pops, int32_t npops, const 
     }
     int rc = ensure_counters(P, 1);
     if (rc == NEAT_OK) rc = layout(P, s);
-    if (rc == NEAT_OK && o.autotune && !P->hb.empty()) rc = autotune(P, s);
+    if (rc == NEAT_OK && o.autotune && !P->hb.empty())
+        rc = tune_block ? autotune_block_threads(P, s) : autotune(P, s, nullptr);
     if (rc == NEAT_OK) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "neat_plan_create: synchronize");
@@ -796,10 +851,11 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
     int cta = 0;
     for (int i = 0; i < nb; ++i) {
         const neat_pop_desc &pd = pops[order[i]];
-        const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch);
+        const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch, NT);
         const uint32_t rec = record_max_bytes(pd.dims.num_inputs, pd.dims.num_outputs, pd.dims.max_nodes,
                                               pd.dims.max_conns);
         const size_t reg = ((size_t)rec + 4u * (size_t)((pd.dims.max_nodes * sh.tile + 3) & ~3) + 15) & ~(size_t)15;
+        if (!shape_ok(sh, NT)) return invalid("neat_forward_multi_noalloc: invalid launch shape");
         int gpc = NT / sh.G;
         if (sh.G > 32) gpc = std::min(gpc, 15);
         while (gpc > 1 && reg * gpc > 200u * 1024u) --gpc;
@@ -867,10 +923,11 @@ namespace neat {
 int fill_population_bucket(const neat_pop_desc &pd, const int32_t *gidx_dev, int block_threads, int cta_begin,
                            BucketDev *out, size_t *footprint)
 {
-    const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch);
+    const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch, block_threads);
     const uint32_t rec = record_max_bytes(pd.dims.num_inputs, pd.dims.num_outputs, pd.dims.max_nodes,
                                           pd.dims.max_conns);
     const size_t reg = ((size_t)rec + 4u * (size_t)((pd.dims.max_nodes * sh.tile + 3) & ~3) + 15) & ~(size_t)15;
+    if (!shape_ok(sh, block_threads)) return invalid("invalid launch shape for a population bucket");
     int gpc = block_threads / sh.G;
     if (sh.G > 32) gpc = std::min(gpc, 15);
     while (gpc > 1 && reg * gpc > 200u * 1024u) --gpc;

@@ -185,6 +185,13 @@ extern "C" int neat_default_launch_recurrent(int32_t pop, neat_dims d, int32_t b
         int g = 8;
         while (g < d.max_nodes - d.num_inputs && g < 128) g <<= 1;
         L.group = g;
+    } else {
+        // two value tiles (current and next iteration) beside the record
+        const size_t rec = record_max_bytes(d.num_inputs, d.num_outputs, d.max_nodes, d.max_conns);
+        while (L.tile > 1 && rec + 8u * (size_t)d.max_nodes * L.tile > kMaxGroupSmem) {
+            L.tile >>= 1;
+            L.group >>= 1;
+        }
     }
     const size_t per_group = record_max_bytes(d.num_inputs, d.num_outputs, d.max_nodes, d.max_conns) +
                              8u * (size_t)((d.max_nodes * L.tile + 3) & ~3);

@@ -49,10 +49,11 @@ def test_host_only_entry_points(lib_path):
     assert neat.neat_record_stride(neat.dims(3, 0, 10, 4)) == 0            # no outputs
     assert neat.neat_record_stride(neat.dims(8, 4, 10, 4)) == 0            # I + O > Nmax
     assert neat.neat_record_stride(neat.dims(1, 1, 4, 8193)) == 0          # too many conns
-    for B in (1, 4, 64, 256):
-        for N in (10, 50, 256, 1024):
+    for B in (1, 2, 4, 17, 64, 256):
+        for N in (10, 50, 100, 256, 300, 511, 1024):
             L = neat.neat_default_launch(1000, neat.dims(4, 2, N, 4 * N), B)
             assert L.group >= L.tile and L.group * L.groups_per_block <= 1024
+            assert L.group & (L.group - 1) == 0 and L.tile & (L.tile - 1) == 0     # the kernels index by shifts
 
 
 def test_argument_errors_do_not_touch_the_device(lib_path):

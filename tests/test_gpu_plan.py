@@ -103,6 +103,10 @@ def test_plan_full_size_uneven_batch_sampled(neat):
     plan = neat.Plan(descs, autotune=True)
     plan.forward(0)
     torch.cuda.synchronize()
+    desc = plan.describe()
+    assert desc["block_threads"] in (256, 512, 1024)                  # tuned, the block size too
+    assert {"block_threads": desc["block_threads"]}.items() <= desc["autotune"][-1].items()
+    assert all(b["G"] <= desc["block_threads"] for b in desc["buckets"])
     worst = 0.0
     for j, (p, dsc) in enumerate(zip(pops, descs)):
         idx = np.random.default_rng(j).choice(p.pop, 48, replace=False)
