@@ -84,3 +84,30 @@ def test_cppn_shared_memory_at_the_default_limit(neat):
     q = np.stack([rng.integers(0, 40, 4000), rng.integers(0, 2, 4000), rng.integers(0, 256, 4000),
                   rng.integers(0, 256, 4000)], 1).astype(np.int32)
     _check(w, pop, q[np.argsort(q[:, 0], kind="stable")], 16)
+
+
+@pytest.mark.parametrize("nmax,cmax", [(32, 96), (64, 200), (150, 400)])
+def test_cppn_equals_forward_bit_for_bit(neat, nmax, cmax):
+    """Over genomes with every activation and aggregation and value tiles of
+    32 to 150 rows, the query kernel's raw outputs equal neat_forward's on
+    the same coordinate inputs bit for bit, including the ragged last chunk
+    (625 queries per block), and match the oracle."""
+    import torch
+    res, P = 5, 24
+    pop = W.random_dag_population(11, P, 5, 1, nmax, cmax, hidden=lambda r: int(r.integers(0, nmax - 5)),
+                                  edges=lambda r, n: int(r.integers(n, 2 * n + 1)), acts=W.ALL_ACTS,
+                                  aggs=W.ALL_AGGS, p_disabled=0.1)
+    d = neat.dims(5, 1, nmax, cmax)
+    rec, st = neat.neat_transform(torch.from_numpy(pop.nodes).cuda(), torch.from_numpy(pop.conns).cuda(), d)
+    w = neat.neat_cppn_query(rec, P, d, res, 2, 0.0).cpu().numpy()          # threshold 0: raw outputs
+    coord = (-1.0 + 2.0 * np.arange(res) / (res - 1)).astype(np.float32)
+    node = np.arange(res * res)
+    xs, ys = coord[node % res], coord[node // res]
+    s, t = np.meshgrid(node, node, indexing="ij")
+    x = np.stack([xs[s.ravel()], ys[s.ravel()], xs[t.ravel()], ys[t.ravel()], np.ones(s.size, np.float32)], 1)
+    xb = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(x, (P,) + x.shape))).cuda()
+    y = neat.neat_forward(rec, P, d, xb).cpu().numpy()[:, :, 0]
+    np.testing.assert_array_equal(w[:, 0].reshape(P, -1), y)
+    g, b, ss, tt = np.meshgrid(np.arange(P), [0], np.arange(0, 25, 3), np.arange(25), indexing="ij")
+    q = np.stack([g.ravel(), b.ravel(), ss.ravel(), tt.ravel()], 1).astype(np.int32)
+    _check(w, pop, q, res, thr=0.0)
