@@ -127,6 +127,20 @@ def test_transform_max_sizes(neat):
     assert_outputs_close(y, oracle.forward(pop.nodes, pop.conns, 16, 8, x), what="max sizes")
 
 
+def test_forward_max_sizes_with_64_inputs(neat):
+    """Nmax 1024, Cmax 8192, 64 input vectors per genome: a 32-column value
+    tile would not fit one block beside the 84 KB record, so the default
+    launch halves the tile; the outputs match the oracle."""
+    pop = W.random_dag_population(4, 6, 16, 8, 1024, 8192, hidden=lambda r: 1000,
+                                  edges=lambda r, n: 8192, acts=W.ALL_ACTS, aggs=W.ALL_AGGS)
+    d, rec = _check_transform(neat, pop, "max, 64 inputs")
+    L = neat.neat_default_launch(6, d, 64)
+    assert L.tile == 16 and L.group == 256
+    x = W.normal_inputs(4, (6, 64, 16))
+    y = neat.neat_forward(rec, 6, d, _dev(x)).cpu().numpy()
+    assert_outputs_close(y, oracle.forward(pop.nodes, pop.conns, 16, 8, x), what="max sizes, 64 inputs")
+
+
 # --------------------------------------------------------------- forward
 
 def test_forward_xor(neat):

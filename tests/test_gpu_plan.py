@@ -31,14 +31,19 @@ def _setup(neat, pops, batch, steps=None, seed=0):
     return out
 
 
-@pytest.mark.parametrize("size_buckets,autotune", [(True, False), (False, False), (True, True)])
-def test_plan_matches_forward_batched_uneven(neat, size_buckets, autotune):
+@pytest.mark.parametrize("size_buckets,autotune,block_threads",
+                         [(True, False, 0), (False, False, 0), (True, True, 0), (True, False, 512),
+                          (True, False, 1024), (False, True, 1024)])
+def test_plan_matches_forward_batched_uneven(neat, size_buckets, autotune, block_threads):
     import torch
     pops = W.batched_populations(0, pop=160)
     descs = _setup(neat, pops, 64)
-    plan = neat.Plan(descs, autotune=autotune, size_buckets=size_buckets)
+    plan = neat.Plan(descs, autotune=autotune, size_buckets=size_buckets, block_threads=block_threads)
     info = plan.describe()
     assert len(info["buckets"]) >= 4
+    if block_threads:
+        assert info["block_threads"] == block_threads
+    assert all(b["G"] <= info["block_threads"] and b["G"] & (b["G"] - 1) == 0 for b in info["buckets"])
     plan.forward(0)
     torch.cuda.synchronize()
     for p, dsc in zip(pops, descs):

@@ -232,6 +232,23 @@ def test_recurrent_ant_full_population(neat):
     _assert_close_conditioned(y[idx], ref, sub.nodes, sub.conns, 27, 8, x[idx], 8, "ant recurrent")
 
 
+def test_recurrent_max_sizes_with_64_inputs(neat):
+    """Nmax 1024, Cmax 8192, 64 input vectors: the default launch halves the
+    tile until the record and both value tiles fit one block (8 columns
+    here); the outputs match the oracle."""
+    pop = W.random_recurrent_population(12, 4, 16, 8, 1024, 8192, hidden=lambda r: 1000,
+                                        edges=lambda r, n: 8192, acts=BOUNDED, aggs=(W.AGG_SUM, W.AGG_MEAN, W.AGG_MAX),
+                                        p_disabled=0.1)
+    d = _dims(neat, pop)
+    L = neat.neat_default_launch_recurrent(4, d, 64)
+    assert L.tile == 8 and L.group == 128
+    x = W.normal_inputs(13, (4, 64, 16))
+    _, st, y = _run(neat, pop.nodes, pop.conns, 16, 8, x, 3)
+    ref, ref_st = oracle.forward_recurrent(pop.nodes, pop.conns, 16, 8, x, 3)
+    np.testing.assert_array_equal(st, ref_st)
+    _assert_close_conditioned(y, ref, pop.nodes, pop.conns, 16, 8, x, 3, "recurrent max sizes, 64 inputs")
+
+
 def test_recurrent_launch_shapes_bit_identical(neat):
     """Every valid launch shape (group, tile, groups per block, PDL) gives the
     same bits as the default launch."""
