@@ -231,8 +231,13 @@ typedef struct neat_launch {
  */
 NEAT_API int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims d, int32_t *order_dev, void *stream);
 
-/* The launch shape neat_forward uses for (pop, d, batch): the smallest
- * number of waves on the current device, genomes spread evenly over its SMs. */
+/* The launch shape neat_forward uses for (pop, d, batch): for one input
+ * vector per genome, 8 to 32 threads per genome by max_nodes; for several,
+ * tiles of up to 32 vectors with a power of two of threads per tile row
+ * (about one per 32 nodes, at most 16), the tile halved until a group's
+ * record and value tile fit one block; then the number of groups per block
+ * giving the fewest waves on the current device, genomes spread evenly over
+ * its SMs. */
 NEAT_API int neat_default_launch(int32_t pop, neat_dims d, int32_t batch, neat_launch *out_host);
 
 /* neat_forward with an explicit launch shape (NULL = default). */
