@@ -94,13 +94,13 @@ plan_kernel(const BucketDev *__restrict__ buckets, int nb, int item_lo, int item
 }
 
 struct Shape {
-    int G, tile, split;
+    int G = 0, tile = 0, split = 1;
 };
 
 struct HostBucket {
-    int pop_index;
-    int n_class;             // node-count bound of the bucket
-    int max_used;            // largest record (bytes) in the bucket
+    int pop_index = 0;
+    int n_class = 0;         // node-count bound of the bucket
+    int max_used = 0;        // largest record (bytes) in the bucket
     std::vector<int32_t> gidx;
     Shape shape;
 };
