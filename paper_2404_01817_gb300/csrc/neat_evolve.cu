@@ -458,7 +458,10 @@ extern "C" int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat
                         (size_t)a.N + 16u;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(mutate_kernel), smem, "neat_mutate: shared memory");
     if (rc) return rc;
-    const int threads = (a.N <= 64 && a.C <= 256) ? 128 : kEvoThreads;
+    // small genomes: two warps (its block-wide steps are barrier-bound, and
+    // more genomes share an SM; 10 000 Ant-sized genomes: 0.094 -> 0.089 ms
+    // against four warps)
+    const int threads = (a.N <= 64 && a.C <= 256) ? 64 : kEvoThreads;
     mutate_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_mutate: launch");
