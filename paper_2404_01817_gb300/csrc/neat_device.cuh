@@ -38,6 +38,8 @@ __device__ __forceinline__ float activate(uint32_t act, float z)
 
 // Programmatic dependent launch controls (PTX griddepcontrol).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Hint: bring the 128-byte line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // A node or connection key: an exact integer in [0, 2^24).

@@ -66,6 +66,14 @@ __global__ void __launch_bounds__(1024, 1) forward_kernel(const ForwardArgs a)
         bulk_g2s(smem_addr(srec), grec, bytes, bar);
     }
     if constexpr (PDL) {
+        // the item's inputs into L2 while the previous kernel finishes, so
+        // that their loads after the wait are L2 hits.  Only a hint: L2 is
+        // the point of coherence, so whatever the previous kernel writes to
+        // them is what the loads after the wait see (no L1 line is filled)
+        const char *xp = reinterpret_cast<const char *>(a.x + ((size_t)g * a.B + b0) * a.I);
+        const int nbytes = bt * a.I * 4;
+        for (int off = lane * 128; off < nbytes; off += G * 128) prefetch_l2(xp + off);
+        if (lane == G - 1 && nbytes > 0) prefetch_l2(xp + nbytes - 1);
         pdl_wait();
         pdl_trigger();
     }
