@@ -891,51 +891,63 @@ def main():
     value_plain = world * POP * S * n_plain / t_plain
 
     # ---- end to end through the C ABI: host genome tensors and observations
-    # in, actions out, every episode.  The episode is cut into chunks of 100
-    # steps: chunk c+1's observations upload on a copy stream while chunk c
-    # runs, and chunk c's actions download behind it.
+    # in, actions out, every episode.  The episode is cut into chunks (a short
+    # first one, so compute starts early): chunk c's observations upload on a
+    # copy stream as soon as the previous episode's chunk c has been consumed
+    # (its forward and its action download), so uploads run ahead of the
+    # compute, and chunk c's actions download behind it.
     nodes_h = torch.from_numpy(pop.nodes).pin_memory()
     conns_h = torch.from_numpy(pop.conns).pin_memory()
     obs_h = obs.cpu().pin_memory()
     act_h = torch.empty(act.shape, dtype=torch.float32).pin_memory()
-    CH = 10 if S % 10 == 0 else 1
-    per = S // CH
+    bounds = [0, min(S, 10)] + [b for b in range(100, S, 100) if b > min(S, 10)] + [S]
+    bounds = sorted(set(bounds))
+    CH = len(bounds) - 1
     chunk_caches = [neat.StepsCache() for _ in range(CH)]
     copy_stream = torch.cuda.Stream(dev)
+    prev_used = [None] * CH      # events: the previous episode is done with chunk c's buffers
 
     def episode_e2e():
         ev_in = [torch.cuda.Event() for _ in range(CH)]
         ev_done = [torch.cuda.Event() for _ in range(CH)]
-        ev_out = torch.cuda.Event()
+        ev_dl = [torch.cuda.Event() for _ in range(CH)]
         nodes.copy_(nodes_h, non_blocking=True)
         conns.copy_(conns_h, non_blocking=True)
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
         neat.neat_schedule(rec, POP, d, order, stream=stream)
-        copy_stream.wait_stream(stream)
         with torch.cuda.stream(copy_stream):
             for c in range(CH):
-                obs[c * per:(c + 1) * per].copy_(obs_h[c * per:(c + 1) * per], non_blocking=True)
+                if prev_used[c] is not None:
+                    copy_stream.wait_event(prev_used[c])
+                lo, hi = bounds[c], bounds[c + 1]
+                obs[lo:hi].copy_(obs_h[lo:hi], non_blocking=True)
                 ev_in[c].record(copy_stream)
         for c in range(CH):
+            lo, hi = bounds[c], bounds[c + 1]
             stream.wait_event(ev_in[c])
-            neat.neat_forward_steps(rec, POP, d, obs[c * per:(c + 1) * per], act[c * per:(c + 1) * per],
-                                    chunk_caches[c], launch=L_batched, stream=stream)
+            neat.neat_forward_steps(rec, POP, d, obs[lo:hi], act[lo:hi], chunk_caches[c], launch=L_batched,
+                                    stream=stream)
             ev_done[c].record(stream)
         with torch.cuda.stream(copy_stream):
             for c in range(CH):
+                lo, hi = bounds[c], bounds[c + 1]
                 copy_stream.wait_event(ev_done[c])
-                act_h[c * per:(c + 1) * per].copy_(act[c * per:(c + 1) * per], non_blocking=True)
-            ev_out.record(copy_stream)
-        stream.wait_event(ev_out)
+                act_h[lo:hi].copy_(act[lo:hi], non_blocking=True)
+                ev_dl[c].record(copy_stream)
+        for c in range(CH):
+            prev_used[c] = ev_dl[c]          # after the download, which follows the forward
+        return ev_dl[CH - 1]
 
-    episode_e2e()
+    last = episode_e2e()
+    stream.wait_event(last)
     torch.cuda.synchronize(dev)
     n_e2e = max(1, min(args.steps, 10))
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(n_e2e):
-        episode_e2e()
+        last = episode_e2e()
+    stream.wait_event(last)                  # every action download of every episode is inside
     e1.record(stream)
     barrier()
     t_e2e = reduce_max(e0.elapsed_time(e1) / 1e3)
@@ -999,8 +1011,9 @@ def main():
                        "step_mean_batched": statistics.mean(fw_ms) / S},
         "e2e": {"value": world * POP * S * n_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
-                "form": f"pinned host genomes and observations in, actions out; {CH} chunks of {per} steps, "
-                        "uploads and downloads overlapped with the graphs on a copy stream"},
+                "form": f"pinned host genomes and observations in, actions out, every episode; {CH} chunks "
+                        f"(the first {bounds[1]} steps, then up to 100): uploads run ahead of the graphs on a copy "
+                        "stream (a chunk's waits for the previous episode to be done with it), downloads behind"},
         "fused_multistep": {"value": world * POP * S * n_fused / t_fused, "unit": UNIT, "episodes": n_fused,
                             "us_per_step": t_fused / n_fused / S * 1e6,
                             "form": "one launch per episode (neat_forward_fused), records read once; valid only "
