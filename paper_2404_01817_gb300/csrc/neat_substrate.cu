@@ -11,11 +11,14 @@
 // runs on the FP32 pipes at the bandwidth roofline rather than on tensor
 // cores, which would also round the weights below the float tolerance.  One
 // block per (genome, batch chunk of NB vectors): each thread owns VEC
-// adjacent target columns of one slice of the source range, streams its
-// weight rows with VEC-wide read-only loads (coalesced across the block),
-// keeps NB x VEC accumulators in registers, and the slices are summed in a
-// fixed order through shared memory, where the layer's values also stay, so
-// the result is a function of the inputs alone.
+// adjacent target columns of one slice of the sources (the slices are
+// equal runs of consecutive rows), keeps NB x VEC accumulators in registers,
+// and the slices are summed in a fixed order through shared memory, where
+// the layer's values also stay, so the result is a function of the inputs
+// alone.  For up to 4 vectors per genome the weights stream through shared
+// memory by TMA bulk copies of whole source rows (substrate_tma_kernel, at
+// the HBM roofline); for larger batches each thread streams its weight rows
+// with VEC-wide read-only loads (substrate_kernel).  Both give the same bits.
 #include <algorithm>
 
 #include "neat_device.cuh"
@@ -35,7 +38,10 @@ struct SubArgs {
     int hidden_act, output_act;
     int groups;            // slices of the source range (threads per column group)
     int cols;              // column groups per pass (cols * groups <= threads)
+    int stage_rows;        // bulk-copy path: source rows per shared-memory stage
 };
+
+__device__ unsigned int g_substrate_error;
 
 template <int VEC>
 struct VecT;
@@ -118,11 +124,149 @@ __global__ void __launch_bounds__(kSubThreads) substrate_kernel(const SubArgs a)
     for (int i = tid; i < nb * R; i += kSubThreads) yg[i] = cur[i];
 }
 
+// The same layers with the weights streamed through shared memory by bulk
+// copies (TMA): each stage is `stage_rows` consecutive source rows, which
+// are contiguous in the source-major block; two stages are in flight, each
+// completing on its own mbarrier (bounded waits).  The sources are split
+// into `groups` slices (equal runs of consecutive rows) and a stage holds
+// the next stage_rows / groups rows of every slice, one bulk copy each, so
+// every thread works on every stage: thread (col, grp) owns the 4 target
+// columns col*4 .. col*4+3 and adds the rows of slice grp, in increasing s,
+// for its NB vectors; the slices' partial sums are added in order through
+// shared memory.  The operations and their order are those of
+// substrate_kernel, so the bits are the same.  Needs R % 4 == 0, R / 4
+// dividing the block, and the per-slice stage rows dividing the slice.
+template <int NB>
+__global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int failed;
+    const int R = a.R, rows = a.stage_rows;
+    float *stage = sm;                                      // [2][rows][R]
+    float *cur = stage + 2 * (size_t)rows * R;              // [NB][R]
+    float *nxt = cur + NB * R;                              // [NB][R]
+    float *part = nxt + NB * R;                             // [groups][NB][R]
+    const int g = blockIdx.x, b0 = blockIdx.y * NB;
+    const int nb = min(NB, a.B - b0);
+    const int tid = threadIdx.x;
+    const int ncols = R / 4, groups = kSubThreads / ncols;
+    const int slen = R / groups;                            // sources per slice (R % groups == 0)
+    const int col = tid % ncols, grp = tid / ncols;
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    const int rps = rows / groups;                          // rows of each slice per stage
+    const uint32_t slice_bytes = (uint32_t)rps * (uint32_t)R * 4u;
+    const uint32_t stage_bytes = slice_bytes * (uint32_t)groups;
+    const int nstages = slen / rps;
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        failed = 0;
+    }
+    const float *xg = a.x + ((size_t)g * a.B + b0) * R;
+    for (int i = tid; i < NB * R; i += kSubThreads) cur[i] = (i < nb * R) ? __ldg(xg + i) : 0.0f;
+    __syncthreads();
+    // copies issued into and completions seen on each buffer (every thread
+    // counts; thread 0 issues)
+    uint32_t issued0 = 0u, issued1 = 0u, seen0 = 0u, seen1 = 0u;
+    // stage st of layer block Wl: rows st*rps .. st*rps+rps-1 of every slice
+    // (one bulk copy per slice), slice j's rows at buffer rows j*rps ..
+    auto issue = [&](int buf, const float *Wl, int st) {
+        if (tid == 0) {
+            fence_proxy_async_smem();                       // the buffer's earlier reads come first
+            const uint32_t bar = buf ? bar1 : bar0;
+            mbar_arrive_expect_tx(bar, stage_bytes);
+            for (int j = 0; j < groups; ++j)
+                bulk_g2s(smem_addr(stage + (size_t)buf * rows * R + (size_t)j * rps * R),
+                         Wl + ((size_t)j * slen + (size_t)st * rps) * R, slice_bytes, bar);
+        }
+        if (buf) ++issued1; else ++issued0;
+    };
+    for (int l = 0; l + 1 < a.L && !failed; ++l) {
+        const float *Wl = a.w + ((size_t)g * (a.L - 1) + l) * (size_t)R * R;
+        const int act = (l + 2 == a.L) ? a.output_act : a.hidden_act;
+        for (int st = 0; st < 2 && st < nstages; ++st) issue(st, Wl, st);
+        float acc[NB][4];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[b][v] = 0.0f;
+        for (int st = 0; st < nstages; ++st) {
+            const int buf = st & 1;
+            if (mbar_wait(buf ? bar1 : bar0, (buf ? seen1 : seen0) & 1u)) {
+                if (buf) ++seen1; else ++seen0;
+            } else {
+                failed = 1;
+            }
+            // this thread's rows: sources grp*slen + st*rps .. + rps - 1
+            const float4 *W4 = reinterpret_cast<const float4 *>(stage + (size_t)buf * rows * R +
+                                                                (size_t)grp * rps * R);
+            const float *xs = cur + grp * slen + st * rps;
+            for (int r = 0; r < rps; ++r) {
+                const float4 w = W4[(size_t)r * ncols + col];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const float xv = xs[b * R + r];
+                    acc[b][0] = fmaf(xv, w.x, acc[b][0]);
+                    acc[b][1] = fmaf(xv, w.y, acc[b][1]);
+                    acc[b][2] = fmaf(xv, w.z, acc[b][2]);
+                    acc[b][3] = fmaf(xv, w.w, acc[b][3]);
+                }
+            }
+            __syncthreads();                                // every thread is done with the buffer
+            if (failed) break;
+            if (st + 2 < nstages) issue(buf, Wl, st + 2);
+        }
+        if (failed) break;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part[((size_t)grp * NB + b) * R + col * 4 + v] = acc[b][v];
+        __syncthreads();
+        for (int i = tid; i < NB * R; i += kSubThreads) {
+            const int b = i / R, t = i - b * R;
+            float sum = part[(size_t)b * R + t];
+            for (int j = 1; j < groups; ++j) sum += part[((size_t)j * NB + b) * R + t];
+            nxt[i] = activate((uint32_t)act, sum);
+        }
+        __syncthreads();
+        float *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    float *yg = a.y + ((size_t)g * a.B + b0) * R;
+    if (failed) {
+        // a stage did not arrive in time: let every copy in flight land
+        // before the block's shared memory is released, then report
+        for (; seen0 < issued0; ++seen0) mbar_wait(bar0, seen0 & 1u);
+        for (; seen1 < issued1; ++seen1) mbar_wait(bar1, seen1 & 1u);
+        if (tid == 0) atomicOr(&g_substrate_error, kErrWaitExpired);
+        for (int i = tid; i < nb * R; i += kSubThreads) yg[i] = __int_as_float(0x7fc00000);
+        return;
+    }
+    for (int i = tid; i < nb * R; i += kSubThreads) yg[i] = cur[i];
+}
+
 template <int NB, int VEC>
 int launch_sub(const SubArgs &a, int pop, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * ((size_t)2 * NB * a.R + (size_t)a.groups * NB * a.R);
     auto kern = substrate_kernel<NB, VEC>;
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_substrate_forward: shared memory");
+    if (rc) return rc;
+    const dim3 grid((unsigned)pop, (unsigned)((a.B + NB - 1) / NB));
+    kern<<<grid, kSubThreads, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_substrate_forward: launch");
+    return NEAT_OK;
+}
+
+template <int NB>
+int launch_tma(const SubArgs &a, int pop, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * (2 * (size_t)a.stage_rows * a.R + 2 * (size_t)NB * a.R +
+                                         (size_t)(kSubThreads / (a.R / 4)) * NB * a.R);
+    auto kern = substrate_tma_kernel<NB>;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_substrate_forward: shared memory");
     if (rc) return rc;
     const dim3 grid((unsigned)pop, (unsigned)((a.B + NB - 1) / NB));
@@ -184,5 +328,47 @@ extern "C" int neat_substrate_forward(const float *weights_dev, int32_t pop, nea
     while (sizeof(float) * ((size_t)2 * nb * a.R + (size_t)a.groups * nb * a.R) > 200u * 1024u && nb > 1) nb >>= 1;
     if (sizeof(float) * ((size_t)3 * nb * a.R) > 200u * 1024u)
         return invalid("neat_substrate_forward: substrate too large for one block");
+    // bulk-copy path: 32 KB stages of whole source rows, when one block
+    // takes the whole batch (at most 4 vectors: each block streams its
+    // genome's weights once), R / 4 divides the block, and the stages,
+    // values and partial sums fit 100 KB (two or more blocks per SM).  Both
+    // kernels split the sources into the same slices, so their results are
+    // identical
+    if (vec4 && kSubThreads % (a.R / 4) == 0 && nb <= 4) {
+        const int groups = kSubThreads / (a.R / 4);
+        // stage rows: about 32 KB, a multiple of the slices, each slice's
+        // share dividing the slice
+        const int slen = a.R / groups;
+        int rows = std::max(groups, std::min(a.R, (32 * 1024) / (4 * a.R)));
+        while (rows > groups && (rows % groups || slen % (rows / groups))) --rows;
+        const int nbt = nb;
+        const size_t smem = sizeof(float) * (2 * (size_t)rows * a.R + 2 * (size_t)nbt * a.R +
+                                             (size_t)groups * nbt * a.R);
+        // the same slices as substrate_kernel: groups = kSubThreads / (R / 4)
+        // there too while its shared memory needs no fewer (true for nb <= 4)
+        if (a.R % groups == 0 && rows % groups == 0 && slen % (rows / groups) == 0 && groups == a.groups &&
+            smem <= 100u * 1024u) {
+            a.stage_rows = rows;
+            switch (nbt) {
+            case 1: return launch_tma<1>(a, pop, as_stream(stream));
+            case 2: return launch_tma<2>(a, pop, as_stream(stream));
+            default: return launch_tma<4>(a, pop, as_stream(stream));
+            }
+        }
+    }
     return vec4 ? launch_vec<4>(a, pop, nb, as_stream(stream)) : launch_vec<1>(a, pop, nb, as_stream(stream));
 }
+
+namespace neat {
+int read_substrate_error(unsigned int *v, int clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_substrate_error, sizeof(*v));
+    if (e != cudaSuccess) return cuda_fail(e, "substrate error word: read");
+    if (clear) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_substrate_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_fail(e, "substrate error word: clear");
+    }
+    return NEAT_OK;
+}
+}  // namespace neat

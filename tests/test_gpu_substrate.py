@@ -43,13 +43,33 @@ def test_other_substrates(neat, res, layers):
     assert_outputs_close(y, oracle.substrate_forward(w, x), what=f"res {res} layers {layers}")
 
 
-def test_batch_chunks_do_not_change_bits(neat):
-    w = _dev(W.substrate_weights(5, 10, res=16, layers=3))
-    x = W.normal_inputs(6, (10, 37, 256))
-    y = neat.neat_substrate_forward(w, _dev(x)).cpu().numpy()
+@pytest.mark.parametrize("res,layers", [(16, 3), (8, 4), (32, 3)])
+def test_batch_chunks_do_not_change_bits(neat, res, layers):
+    """Batches of up to 4 vectors take the bulk-copy kernel, larger ones the
+    per-thread-load kernel; both split the sources into the same slices, so
+    every vector's outputs are the same bits either way."""
+    R = res * res
+    w = _dev(W.substrate_weights(5, 10, res=res, layers=layers, scale=0.15 if R > 256 else 0.3))
+    x = W.normal_inputs(6, (10, 37, R))
+    y = neat.neat_substrate_forward(w, _dev(x), res, layers).cpu().numpy()
+    assert_outputs_close(y, oracle.substrate_forward(w.cpu().numpy(), x), what=f"res {res} layers {layers} batch 37")
     for b in (0, 15, 16, 36):
-        yb = neat.neat_substrate_forward(w, _dev(x[:, b:b + 1])).cpu().numpy()
+        yb = neat.neat_substrate_forward(w, _dev(x[:, b:b + 1]), res, layers).cpu().numpy()
         np.testing.assert_array_equal(yb[:, 0], y[:, b])
+    y4 = neat.neat_substrate_forward(w, _dev(x[:, 3:7]), res, layers).cpu().numpy()
+    np.testing.assert_array_equal(y4, y[:, 3:7])
+
+
+@pytest.mark.parametrize("res,layers,batch", [(8, 2, 1), (8, 4, 3), (32, 3, 1), (32, 2, 2), (16, 5, 4)])
+def test_bulk_copy_substrates_match_oracle(neat, res, layers, batch):
+    """The bulk-copy kernel at one stage per layer (8 x 8), eight-row
+    stages (32 x 32), several layers (the stage barriers' phases carry
+    across layers) and 1 to 4 vectors."""
+    R = res * res
+    w = W.substrate_weights(7, 12, res=res, layers=layers, scale=0.15 if R > 256 else 0.3)
+    x = W.normal_inputs(8, (12, batch, R))
+    y = neat.neat_substrate_forward(_dev(w), _dev(x), res, layers).cpu().numpy()
+    assert_outputs_close(y, oracle.substrate_forward(w, x), what=f"bulk copy res {res} layers {layers} batch {batch}")
 
 
 def test_cppn_to_substrate_end_to_end(neat):
