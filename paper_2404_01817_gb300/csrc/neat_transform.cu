@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
     short *dst_row = src_row + C;
 
     __shared__ unsigned int st, acts_seen, aggs_seen;
-    __shared__ int n_present, n_edges, max_level, changed;
+    __shared__ int n_present, n_edges, max_level;
     if (tid == 0) {
         st = 0;
         acts_seen = 0;
@@ -191,22 +191,21 @@ __global__ void __launch_bounds__(512) transform_kernel(TransformArgs a)
         cnt[r] = indeg[r];
         if (level[r] == -1 && (indeg[r] == 0 || a.recurrent)) level[r] = 0;
     }
+    // one barrier per level: it also tells every thread whether any node
+    // joined the next level
+    __syncthreads();
     for (int L = 0; !a.recurrent; ++L) {
-        if (tid == 0) changed = 0;
-        __syncthreads();
+        int joined = 0;
         for (int c = tid; c < C; c += nt) {
             const int d = dst_row[c];
             if (d >= 0 && level[src_row[c]] == L) {
                 if (atomicSub(&indeg[d], 1) == 1) {
                     level[d] = L + 1;
-                    changed = 1;
+                    joined = 1;
                 }
             }
         }
-        __syncthreads();
-        const int more = changed;
-        __syncthreads();
-        if (!more) break;
+        if (!__syncthreads_or(joined)) break;
     }
     lst = 0;
     int lmax = -1;
