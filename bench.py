@@ -963,7 +963,7 @@ def main():
     fwd_launch_s = statistics.mean(fw_ms) / 1e3 / S                      # per forward, graph-amortised
     achieved = alg_bytes / fwd_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = l2_traffic = None
+    traffic = l2_traffic = warp_insts = None
     prof = os.path.join(ROOT, "profiles", "forward_ant_traffic.json")
     if os.path.exists(prof):
         try:
@@ -971,6 +971,7 @@ def main():
             if tj.get("kernel_hash") == kernel_hash():
                 traffic = tj.get("dram_bytes_per_launch")
                 l2_traffic = tj.get("l2_bytes_per_launch")
+                warp_insts = tj.get("warp_instructions_per_launch")
         except (OSError, ValueError):
             pass
 
@@ -1026,6 +1027,20 @@ def main():
                      "alg_bytes_per_launch": alg_bytes},
         "clocks": clocks.summary(),
     }
+    # the walk is bound by instruction issue, not HBM: the same launch against
+    # the SMs' issue capacity (one warp instruction per cycle per scheduler,
+    # four schedulers per SM, at the SM clock sampled during the timed region)
+    if warp_insts:
+        sm_mhz = line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz")
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        if sm_mhz:
+            issue_peak = 4 * sms * sm_mhz * 1e6
+            issue_achieved = warp_insts / fwd_launch_s
+            line["issue_roofline"] = {
+                "bound": "issue", "achieved": issue_achieved, "peak": issue_peak, "unit": "warp instructions/s",
+                "frac": issue_achieved / issue_peak, "instructions_per_launch": warp_insts,
+                "note": "warp instructions per launch from ncu (smsp__inst_executed.sum, same kernel source); peak = "
+                        f"4 schedulers x {sms} SMs x the sampled SM clock"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pop, obs.cpu().numpy())
     cache.close()
