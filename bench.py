@@ -18,7 +18,14 @@ streams its inputs from HBM; the transformed population (~19 MB) stays
 L2-resident across the steps of an episode, as it would between environment
 steps.
 
+`roofline` rates the forward launch by its algorithmic bytes against the
+measured HBM bandwidth; `issue_roofline` rates the same launch against the
+bound that holds it, instruction issue (warp instructions per launch, from a
+recorded ncu count for the same kernel sources, over 4 schedulers x SMs x the
+sampled SM clock).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --workload xor|batched|cppn|serving|recurrent|distance|evolve|substrate
 """
 from __future__ import annotations
 
