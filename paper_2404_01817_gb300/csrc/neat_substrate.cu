@@ -15,10 +15,11 @@
 // equal runs of consecutive rows), keeps NB x VEC accumulators in registers,
 // and the slices are summed in a fixed order through shared memory, where
 // the layer's values also stay, so the result is a function of the inputs
-// alone.  For up to 4 vectors per genome the weights stream through shared
-// memory by TMA bulk copies of whole source rows (substrate_tma_kernel, at
-// the HBM roofline); for larger batches each thread streams its weight rows
-// with VEC-wide read-only loads (substrate_kernel).  Both give the same bits.
+// alone.  The weights stream through shared memory by TMA bulk copies of
+// whole source rows (substrate_tma_kernel, tiles of up to 4 vectors, near
+// the HBM roofline at one vector per genome); shapes it cannot take (R not a
+// multiple of 4) use per-thread VEC-wide read-only loads (substrate_kernel).
+// Both accumulate compensated dot products and give the same bits.
 #include <algorithm>
 
 #include "neat_device.cuh"
@@ -43,6 +44,43 @@ struct SubArgs {
 
 __device__ unsigned int g_substrate_error;
 
+// Compensated dot products.  Error-free transformations of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005):
+// TwoSum (after Knuth) and TwoProduct by one FMA.  dot2_step adds x*w to the
+// pair (s, c), s the rounded running sum and c the sum of the rounding
+// errors; s + c is as accurate as the dot product in twice the working
+// precision, so sums of large weights stay within the float tolerance.  The
+// _rn intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void dot2_step(float &s, float &c, float x, float w)
+{
+    const float p = __fmul_rn(x, w);
+    const float pe = __fmaf_rn(x, w, -p);                  // x*w - p, exactly
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
+// The slices' (s, c) pairs added in slice order, rounded once at the end.
+__device__ __forceinline__ float combine_slices(const float *ps, const float *pc, size_t stride, int groups)
+{
+    float S = ps[0], C = pc[0];
+    for (int j = 1; j < groups; ++j) {
+        float t, e;
+        two_sum(S, ps[(size_t)j * stride], t, e);
+        S = t;
+        C = __fadd_rn(C, __fadd_rn(e, pc[(size_t)j * stride]));
+    }
+    return __fadd_rn(S, C);
+}
+
 template <int VEC>
 struct VecT;
 template <>
@@ -66,7 +104,8 @@ __global__ void __launch_bounds__(kSubThreads) substrate_kernel(const SubArgs a)
     const int R = a.R;
     float *cur = sm;                       // [NB][R]
     float *nxt = cur + NB * R;             // [NB][R]
-    float *part = nxt + NB * R;            // [groups][NB][R]
+    float *ps = nxt + NB * R;              // [groups][NB][R] slice sums
+    float *pc = ps + (size_t)a.groups * NB * R;   // [groups][NB][R] their rounding errors
     const int g = blockIdx.x, b0 = blockIdx.y * NB;
     const int nb = min(NB, a.B - b0);
     const int tid = threadIdx.x;
@@ -83,11 +122,11 @@ __global__ void __launch_bounds__(kSubThreads) substrate_kernel(const SubArgs a)
         for (int c0 = 0; c0 < ncols; c0 += a.cols) {
             const int c = c0 + col_in_pass;
             if (grp < a.groups && c < ncols) {
-                float acc[NB][VEC];
+                float as[NB][VEC], ac[NB][VEC];
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[b][v] = 0.0f;
+                    for (int v = 0; v < VEC; ++v) as[b][v] = ac[b][v] = 0.0f;
                 const int s0 = grp * slice, s1 = min(R, s0 + slice);
                 const V *col = reinterpret_cast<const V *>(Wl) + c;
 #pragma unroll 8
@@ -97,22 +136,24 @@ __global__ void __launch_bounds__(kSubThreads) substrate_kernel(const SubArgs a)
                     for (int b = 0; b < NB; ++b) {
                         const float xv = cur[b * R + s];
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[b][v] = fmaf(xv, VecT<VEC>::get(wv, v), acc[b][v]);
+                        for (int v = 0; v < VEC; ++v) dot2_step(as[b][v], ac[b][v], xv, VecT<VEC>::get(wv, v));
                     }
                 }
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) part[((size_t)grp * NB + b) * R + c * VEC + v] = acc[b][v];
+                    for (int v = 0; v < VEC; ++v) {
+                        ps[((size_t)grp * NB + b) * R + c * VEC + v] = as[b][v];
+                        pc[((size_t)grp * NB + b) * R + c * VEC + v] = ac[b][v];
+                    }
             }
             __syncthreads();
             // sum the slices in order, apply the activation
             for (int i = tid; i < NB * a.cols * VEC; i += kSubThreads) {
                 const int b = i / (a.cols * VEC), t = c0 * VEC + i % (a.cols * VEC);
                 if (t >= R) continue;
-                float s = part[(size_t)b * R + t];
-                for (int j = 1; j < a.groups; ++j) s += part[((size_t)j * NB + b) * R + t];
-                nxt[b * R + t] = activate((uint32_t)act, s);
+                nxt[b * R + t] = activate((uint32_t)act, combine_slices(ps + (size_t)b * R + t, pc + (size_t)b * R + t,
+                                                                         (size_t)NB * R, a.groups));
             }
             __syncthreads();
         }
@@ -146,7 +187,8 @@ __global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArg
     float *stage = sm;                                      // [2][rows][R]
     float *cur = stage + 2 * (size_t)rows * R;              // [NB][R]
     float *nxt = cur + NB * R;                              // [NB][R]
-    float *part = nxt + NB * R;                             // [groups][NB][R]
+    float *ps = nxt + NB * R;                               // [groups][NB][R] slice sums
+    float *pc = ps + (size_t)(kSubThreads / (R / 4)) * NB * R;   // [groups][NB][R] their rounding errors
     const int g = blockIdx.x, b0 = blockIdx.y * NB;
     const int nb = min(NB, a.B - b0);
     const int tid = threadIdx.x;
@@ -186,11 +228,11 @@ __global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArg
         const float *Wl = a.w + ((size_t)g * (a.L - 1) + l) * (size_t)R * R;
         const int act = (l + 2 == a.L) ? a.output_act : a.hidden_act;
         for (int st = 0; st < 2 && st < nstages; ++st) issue(st, Wl, st);
-        float acc[NB][4];
+        float as[NB][4], ac[NB][4];
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[b][v] = 0.0f;
+            for (int v = 0; v < 4; ++v) as[b][v] = ac[b][v] = 0.0f;
         for (int st = 0; st < nstages; ++st) {
             const int buf = st & 1;
             if (mbar_wait(buf ? bar1 : bar0, (buf ? seen1 : seen0) & 1u)) {
@@ -207,10 +249,10 @@ __global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArg
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const float xv = xs[b * R + r];
-                    acc[b][0] = fmaf(xv, w.x, acc[b][0]);
-                    acc[b][1] = fmaf(xv, w.y, acc[b][1]);
-                    acc[b][2] = fmaf(xv, w.z, acc[b][2]);
-                    acc[b][3] = fmaf(xv, w.w, acc[b][3]);
+                    dot2_step(as[b][0], ac[b][0], xv, w.x);
+                    dot2_step(as[b][1], ac[b][1], xv, w.y);
+                    dot2_step(as[b][2], ac[b][2], xv, w.z);
+                    dot2_step(as[b][3], ac[b][3], xv, w.w);
                 }
             }
             __syncthreads();                                // every thread is done with the buffer
@@ -221,13 +263,15 @@ __global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArg
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) part[((size_t)grp * NB + b) * R + col * 4 + v] = acc[b][v];
+            for (int v = 0; v < 4; ++v) {
+                ps[((size_t)grp * NB + b) * R + col * 4 + v] = as[b][v];
+                pc[((size_t)grp * NB + b) * R + col * 4 + v] = ac[b][v];
+            }
         __syncthreads();
         for (int i = tid; i < NB * R; i += kSubThreads) {
             const int b = i / R, t = i - b * R;
-            float sum = part[(size_t)b * R + t];
-            for (int j = 1; j < groups; ++j) sum += part[((size_t)j * NB + b) * R + t];
-            nxt[i] = activate((uint32_t)act, sum);
+            nxt[i] = activate((uint32_t)act, combine_slices(ps + (size_t)b * R + t, pc + (size_t)b * R + t,
+                                                             (size_t)NB * R, groups));
         }
         __syncthreads();
         float *tmp = cur;
@@ -250,7 +294,7 @@ __global__ void __launch_bounds__(kSubThreads) substrate_tma_kernel(const SubArg
 template <int NB, int VEC>
 int launch_sub(const SubArgs &a, int pop, cudaStream_t s)
 {
-    const size_t smem = sizeof(float) * ((size_t)2 * NB * a.R + (size_t)a.groups * NB * a.R);
+    const size_t smem = sizeof(float) * ((size_t)2 * NB * a.R + 2 * (size_t)a.groups * NB * a.R);
     auto kern = substrate_kernel<NB, VEC>;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_substrate_forward: shared memory");
     if (rc) return rc;
@@ -265,7 +309,7 @@ template <int NB>
 int launch_tma(const SubArgs &a, int pop, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * (2 * (size_t)a.stage_rows * a.R + 2 * (size_t)NB * a.R +
-                                         (size_t)(kSubThreads / (a.R / 4)) * NB * a.R);
+                                         2 * (size_t)(kSubThreads / (a.R / 4)) * NB * a.R);
     auto kern = substrate_tma_kernel<NB>;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_substrate_forward: shared memory");
     if (rc) return rc;
@@ -323,31 +367,32 @@ extern "C" int neat_substrate_forward(const float *weights_dev, int32_t pop, nea
     int nb = 1;
     while (nb < batch && nb < 16) nb <<= 1;
     // shared memory: two value tiles and the slice partials
-    while (sizeof(float) * ((size_t)2 * nb * a.R + (size_t)a.groups * nb * a.R) > 200u * 1024u && a.groups > 1)
+    while (sizeof(float) * ((size_t)2 * nb * a.R + 2 * (size_t)a.groups * nb * a.R) > 200u * 1024u && a.groups > 1)
         a.groups >>= 1;
-    while (sizeof(float) * ((size_t)2 * nb * a.R + (size_t)a.groups * nb * a.R) > 200u * 1024u && nb > 1) nb >>= 1;
-    if (sizeof(float) * ((size_t)3 * nb * a.R) > 200u * 1024u)
+    while (sizeof(float) * ((size_t)2 * nb * a.R + 2 * (size_t)a.groups * nb * a.R) > 200u * 1024u && nb > 1)
+        nb >>= 1;
+    if (sizeof(float) * ((size_t)4 * nb * a.R) > 200u * 1024u)
         return invalid("neat_substrate_forward: substrate too large for one block");
-    // bulk-copy path: 32 KB stages of whole source rows, when one block
-    // takes the whole batch (at most 4 vectors: each block streams its
-    // genome's weights once), R / 4 divides the block, and the stages,
-    // values and partial sums fit 100 KB (two or more blocks per SM).  Both
-    // kernels split the sources into the same slices, so their results are
-    // identical
-    if (vec4 && kSubThreads % (a.R / 4) == 0 && nb <= 4) {
+    // bulk-copy path: 32 KB stages of whole source rows, tiles of up to 4
+    // vectors (with the compensated sums, larger batches are bound by
+    // arithmetic, not by streaming the weights once per tile), when R / 4
+    // divides the block and the stages, values and partial sums fit 112 KB
+    // (two or more blocks per SM).  Both kernels split the sources into the
+    // same slices, so their results are identical
+    if (vec4 && kSubThreads % (a.R / 4) == 0) {
         const int groups = kSubThreads / (a.R / 4);
         // stage rows: about 32 KB, a multiple of the slices, each slice's
         // share dividing the slice
         const int slen = a.R / groups;
         int rows = std::max(groups, std::min(a.R, (32 * 1024) / (4 * a.R)));
         while (rows > groups && (rows % groups || slen % (rows / groups))) --rows;
-        const int nbt = nb;
+        const int nbt = std::min(nb, 4);
         const size_t smem = sizeof(float) * (2 * (size_t)rows * a.R + 2 * (size_t)nbt * a.R +
-                                             (size_t)groups * nbt * a.R);
+                                             2 * (size_t)groups * nbt * a.R);
         // the same slices as substrate_kernel: groups = kSubThreads / (R / 4)
         // there too while its shared memory needs no fewer (true for nb <= 4)
         if (a.R % groups == 0 && rows % groups == 0 && slen % (rows / groups) == 0 && groups == a.groups &&
-            smem <= 100u * 1024u) {
+            smem <= 112u * 1024u) {
             a.stage_rows = rows;
             switch (nbt) {
             case 1: return launch_tma<1>(a, pop, as_stream(stream));

@@ -193,3 +193,31 @@ def test_random_words(neat):
     assert abs(v.mean() / 2**32 - 0.5) < 0.002
     bits = np.unpackbits(a.cpu().numpy().view(np.uint8))
     assert abs(bits.mean() - 0.5) < 0.001
+
+
+def test_full_generation_at_bench_size_sampled(neat):
+    """The evolve workload as bench.py runs it: 10 000 Ant-shaped genomes in
+    mid-evolution, random parent pairs, device-generated Philox words and
+    normals, crossover, mutation with the appendix's settings, transform.
+    Sampled children against the oracle's crossover and mutation on the same
+    words; every child valid and acyclic."""
+    import torch
+    P = 10000
+    p = W.ant_related_population(0, P, acyclic=True)
+    d = neat.dims(27, 8, 50, 200)
+    nodes, conns = _dev(p.nodes), _dev(p.conns)
+    parents = np.random.default_rng(5).integers(0, P, size=(P, 2)).astype(np.int32)
+    Wn, Zn = neat.neat_mutation_sizes(d)
+    xw = neat.neat_fill_words(11, 0, torch.empty((P, 250), dtype=torch.int32, device="cuda"))
+    mw = neat.neat_fill_words(11, 1, torch.empty((P, Wn), dtype=torch.int32, device="cuda"))
+    z = neat.neat_fill_normal(11, 0, torch.empty((P, Zn), device="cuda"))
+    keys = np.arange(1000, 1000 + P, dtype=np.int32)
+    g_cfg, o_cfg = _configs(neat, **PAPER)
+    cn, cc = neat.neat_crossover(nodes, conns, d, _dev(parents), xw)
+    neat.neat_mutate(cn, cc, d, g_cfg, mw, z, _dev(keys))
+    rec, status = neat.neat_transform(cn, cc, d)
+    assert (status.cpu().numpy() & 0xFF == 0).all()
+    idx = np.arange(0, P, 97)
+    on, oc = oracle.crossover(p.nodes, p.conns, parents[idx], xw.cpu().numpy().view(np.uint32)[idx])
+    on, oc = oracle.mutate(on, oc, 27, 8, o_cfg, mw.cpu().numpy().view(np.uint32)[idx], z.cpu().numpy()[idx], keys[idx])
+    _compare(cn.cpu().numpy()[idx], cc.cpu().numpy()[idx], on, oc, "full generation sample")

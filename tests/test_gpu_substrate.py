@@ -96,3 +96,24 @@ def test_cppn_to_substrate_end_to_end(neat):
             compared += 1
     assert compared >= 2
     torch.cuda.synchronize()
+
+
+def test_full_size_bench_launch_sampled(neat):
+    """The substrate workload as bench.py runs it: 1000 CPPN genomes queried on
+    3 layers of 16 x 16 (524 MB of weight blocks), one vector per genome (the
+    bulk-copy kernel, 1000 blocks), and 16 vectors (the per-thread-load
+    kernel); sampled genomes against the oracle on the same weight blocks."""
+    import torch
+    pop = W.cppn_population(0, 1000)
+    d = neat.dims(5, 1, pop.max_nodes, pop.max_conns)
+    rec, _ = neat.neat_transform(_dev(pop.nodes), _dev(pop.conns), d)
+    w = neat.neat_cppn_query(rec, 1000, d, 16, 3, 0.2)
+    idx = np.arange(0, 1000, 41)
+    wi = w[torch.from_numpy(idx).cuda()].cpu().numpy()
+    for batch in (1, 16):
+        x = W.normal_inputs(20 + batch, (1000, batch, 256))
+        y = neat.neat_substrate_forward(w, _dev(x)).cpu().numpy()
+        assert_outputs_close(y[idx], oracle.substrate_forward(wi, x[idx]), what=f"full size batch {batch}")
+        if batch == 16:
+            y1 = neat.neat_substrate_forward(w, _dev(x[:, :1])).cpu().numpy()
+            np.testing.assert_array_equal(y1[:, 0], y[:, 0])          # both kernels, the same bits
