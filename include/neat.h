@@ -491,8 +491,14 @@ NEAT_API int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_dims
  * layer).  Layer l+1 node t = act(sum_s W_l[s][t] v_l[s]), no bias;
  * act = hidden_act for inner layers, output_act for the last (ids as for
  * nodes).  The paper gives no substrate rule; this is this library's.
- * Float arithmetic, source sums split into at most a fixed number of slices
- * added in order (deterministic).  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+ * Float arithmetic: each source sum is split into a fixed number of slices
+ * of consecutive sources, each a compensated dot product (Dot2, Ogita, Rump
+ * and Oishi, 2005: as accurate as twice the float precision), the slices
+ * added in order with their errors carried, one rounding at the end; the
+ * result is deterministic and does not depend on the batch size.  A weight
+ * stage that does not arrive within the bounded wait gives NaN outputs and
+ * sets the device error word (neat_device_error).  Errors: NEAT_EINVAL,
+ * NEAT_ECUDA. */
 NEAT_API int neat_substrate_forward(const float *weights_dev, int32_t pop, neat_substrate sub, const float *inputs_dev,
                                     int32_t batch, int32_t hidden_act, int32_t output_act, float *outputs_dev,
                                     void *stream);
