@@ -275,8 +275,77 @@ NEAT_API int neat_forward_fused(const void *transformed_dev, int32_t pop, neat_d
                                 int64_t in_step_stride, int32_t batch, float *outputs_dev, int64_t out_step_stride,
                                 int32_t steps, const neat_launch *launch, void *stream);
 
+/* ------------------------------------------------------ lane programs
+ *
+ * The calculation of Section 3.3 for ONE input vector per genome per call
+ * (a control loop that steps every genome once per environment step),
+ * compiled per transformed population into lane programs: one thread
+ * evaluates one genome and the 32 genomes of a warp share one instruction
+ * stream, with no barrier anywhere in the walk.  neat_lanes_pack compiles
+ * (once per transform); neat_forward_lanes / neat_forward_lanes_steps run.
+ * Outputs are bit-identical to neat_forward with batch 1 (same node rule,
+ * same aggregation order; the padding edges of a lane program change no
+ * bit of any partial).  Limits: max_nodes <= 128; records from
+ * neat_transform (feedforward; a genome whose record has no topological
+ * order gets NaN outputs and is counted in neat_lanes_info.unordered).
+ *
+ * Compilation: per genome a list schedule of "beats" of up to two nodes
+ * whose sources are all computed in earlier beats (longest remaining path
+ * first); genomes sorted by (beats, edge quads), deepest first, 32 to a
+ * warp; each warp program holds its beats' node entries and the nodes'
+ * incoming edges in quads of four, interleaved by lane.
+ */
+typedef struct neat_lanes_info {
+    int32_t pop;
+    int32_t warps;              /* ceil(pop / 32): blocks of 32 threads per forward */
+    uint32_t max_warp_bytes;    /* largest warp program: a stage_bytes that stages every program */
+    uint32_t warp_stride;       /* bytes reserved for each warp program */
+    uint32_t unordered;         /* genomes with no feedforward order (NaN outputs) */
+    uint32_t reserved;
+} neat_lanes_info;
+
+/* Bytes of the lanes buffer for `pop` genomes (0 if the dims are invalid or
+ * max_nodes > 128). */
+NEAT_API size_t neat_lanes_bytes(int32_t pop, neat_dims d);
+
+/* Compile the lane programs of `pop` transformed genomes (records of
+ * neat_transform with the same dims) into lanes_dev (caller-owned device
+ * buffer of >= neat_lanes_bytes(pop, d) bytes, 128-byte aligned).  Three
+ * small kernels on `stream`; nothing is allocated.  Recompile after every
+ * transform.  Errors: NEAT_EINVAL (dims, null pointer, alignment),
+ * NEAT_ENOMEM (buffer too small), NEAT_ECUDA. */
+NEAT_API int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_dims d, void *lanes_dev,
+                             size_t lanes_bytes, void *stream);
+
+/* Header of a packed buffer into *out_host (synchronous: a device-to-host
+ * copy on the legacy stream, after the pack has completed). */
+NEAT_API int neat_lanes_query(const void *lanes_dev, neat_lanes_info *out_host);
+
+/* One forward from lane programs: inputs f32 [pop][I] -> outputs f32
+ * [pop][O] (genome order; NaN for genomes with an error bit).  Each warp
+ * program is copied into shared memory when it fits stage_bytes (0: the
+ * smaller of warp_stride and 64 KB); a larger one is read from device
+ * memory (same results, slower).  pop and d must be those of the pack.
+ * Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_forward_lanes(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                float *outputs_dev, uint32_t stage_bytes, void *stream);
+
+/* `steps` forwards from lane programs as one CUDA graph, step s reading
+ * inputs_dev + s * in_step_stride and writing outputs_dev + s *
+ * out_step_stride floats; every step after the first launches with
+ * programmatic dependent launch (its programs are staged while the previous
+ * step drains; its inputs are read after the previous step completes).  The
+ * graph is built on first use, kept in *cache (initialise to NULL; free with
+ * neat_lanes_cache_destroy) and rebuilt when an argument changes.  Repacking
+ * the same lanes buffer between replays is allowed. */
+typedef struct neat_lanes_cache neat_lanes_cache;
+NEAT_API int neat_forward_lanes_steps(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                      int64_t in_step_stride, float *outputs_dev, int64_t out_step_stride,
+                                      int32_t steps, uint32_t stage_bytes, neat_lanes_cache **cache, void *stream);
+NEAT_API void neat_lanes_cache_destroy(neat_lanes_cache *cache);
+
 /*
- * Device error word of the forward (single-step and fused), plan, CPPN, recurrent and distance kernels: bit 0 is set when a
+ * Device error word of the forward (single-step, fused and lane-program), plan, CPPN, recurrent and distance kernels: bit 0 is set when a
  * bounded on-device wait (a record copy into shared memory, 1 s) ran out;
  * the affected outputs are NaN.  Copies the word to *out_host and clears it if `clear`.
  * Synchronous (a device-to-host copy on the legacy stream).

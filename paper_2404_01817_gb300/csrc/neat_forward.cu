@@ -537,15 +537,16 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
         e = cudaMemcpyToSymbol(g_forward_error, &zero, sizeof(zero));
         if (e != cudaSuccess) return cuda_fail(e, "neat_device_error: clear");
     }
-    unsigned int vp = 0, vc = 0, vr = 0, vd = 0, vf = 0, vs = 0;
+    unsigned int vp = 0, vc = 0, vr = 0, vd = 0, vf = 0, vs = 0, vl = 0;
     int rc = read_plan_error(&vp, clear);
     if (rc == NEAT_OK) rc = read_cppn_error(&vc, clear);
     if (rc == NEAT_OK) rc = read_rnn_error(&vr, clear);
     if (rc == NEAT_OK) rc = read_distance_error(&vd, clear);
     if (rc == NEAT_OK) rc = read_fused_error(&vf, clear);
     if (rc == NEAT_OK) rc = read_substrate_error(&vs, clear);
+    if (rc == NEAT_OK) rc = read_lanes_error(&vl, clear);
     if (rc) return rc;
-    *out_host = v | vp | vc | vr | vd | vf | vs;
+    *out_host = v | vp | vc | vr | vd | vf | vs | vl;
     return NEAT_OK;
 }
 

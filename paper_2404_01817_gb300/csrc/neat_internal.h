@@ -129,6 +129,7 @@ int read_rnn_error(unsigned int *v, int clear);    // neat_recurrent.cu
 int read_distance_error(unsigned int *v, int clear);   // neat_distance.cu
 int read_fused_error(unsigned int *v, int clear);      // neat_fused.cu
 int read_substrate_error(unsigned int *v, int clear);  // neat_substrate.cu
+int read_lanes_error(unsigned int *v, int clear);      // neat_lanes.cu
 // Groups per block that put `items` groups of `group` threads, each needing
 // `per_group` bytes of shared memory, in the fewest waves with the busiest SM
 // least loaded (neat_forward.cu).

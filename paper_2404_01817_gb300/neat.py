@@ -120,6 +120,11 @@ def mutation(**kw) -> Mutation:
     return m
 
 
+class LanesInfo(ctypes.Structure):
+    _fields_ = [("pop", _i32), ("warps", _i32), ("max_warp_bytes", ctypes.c_uint32),
+                ("warp_stride", ctypes.c_uint32), ("unordered", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class PlanOptions(ctypes.Structure):
     _fields_ = [("autotune", _i32), ("size_buckets", _i32), ("block_threads", _i32), ("pdl", _i32)]
 
@@ -150,6 +155,13 @@ _sig = {
     "neat_forward_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32,
                                           ctypes.POINTER(Launch), ctypes.POINTER(_P), _P]),
     "neat_steps_cache_destroy": (None, [_P]),
+    "neat_lanes_bytes": (ctypes.c_size_t, [_i32, Dims]),
+    "neat_lanes_pack": (ctypes.c_int, [_P, _i32, Dims, _P, ctypes.c_size_t, _P]),
+    "neat_lanes_query": (ctypes.c_int, [_P, ctypes.POINTER(LanesInfo)]),
+    "neat_forward_lanes": (ctypes.c_int, [_P, _i32, Dims, _P, _P, ctypes.c_uint32, _P]),
+    "neat_forward_lanes_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _P, _i64, _i32, ctypes.c_uint32,
+                                                ctypes.POINTER(_P), _P]),
+    "neat_lanes_cache_destroy": (None, [_P]),
     "neat_forward_fused": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32, ctypes.POINTER(Launch), _P]),
     "neat_plan_create": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, ctypes.POINTER(PlanOptions), _P,
                                         ctypes.POINTER(_P)]),
@@ -481,6 +493,73 @@ def neat_forward_steps(transformed, pop: int, d: Dims, inputs, outputs, cache: S
                                    ctypes.byref(launch) if launch is not None else None,
                                    ctypes.byref(cache.handle), _stream(stream))
     _check(code, "neat_forward_steps")
+    return outputs
+
+
+def neat_lanes_bytes(pop: int, d: Dims) -> int:
+    return int(_lib.neat_lanes_bytes(pop, d))
+
+
+def neat_lanes_pack(transformed, pop: int, d: Dims, lanes=None, stream=None):
+    """Compile lane programs (one thread per genome) of a transformed
+    population; returns the lanes buffer (uint8 CUDA tensor)."""
+    import torch
+    nbytes = neat_lanes_bytes(pop, d)
+    if nbytes == 0:
+        raise NeatError(NEAT_EINVAL, "neat_lanes_bytes (dims not supported by lane programs)")
+    if lanes is None:
+        lanes = torch.empty(nbytes, dtype=torch.uint8, device=transformed.device)
+    _check(_lib.neat_lanes_pack(_ptr(transformed), pop, d, _ptr(lanes), lanes.numel() * lanes.element_size(),
+                                _stream(stream)), "neat_lanes_pack")
+    return lanes
+
+
+def neat_lanes_query(lanes) -> LanesInfo:
+    info = LanesInfo()
+    _check(_lib.neat_lanes_query(_ptr(lanes), ctypes.byref(info)), "neat_lanes_query")
+    return info
+
+
+def neat_forward_lanes(lanes, pop: int, d: Dims, inputs, outputs=None, stage_bytes: int = 0, stream=None):
+    """One forward from lane programs: inputs f32 [P][I] (or [P][1][I]) ->
+    outputs f32 with the same leading shape and O last."""
+    import torch
+    assert inputs.is_contiguous() and inputs.numel() == pop * d.num_inputs
+    if outputs is None:
+        outputs = torch.empty(tuple(inputs.shape[:-1]) + (d.num_outputs,), dtype=torch.float32, device=inputs.device)
+    _check(_lib.neat_forward_lanes(_ptr(lanes), pop, d, _ptr(inputs), _ptr(outputs), stage_bytes, _stream(stream)),
+           "neat_forward_lanes")
+    return outputs
+
+
+class LanesCache:
+    """Owner of the CUDA graph that neat_forward_lanes_steps builds and replays."""
+
+    def __init__(self):
+        self.handle = _P(None)
+
+    def close(self):
+        if self.handle.value:
+            _lib.neat_lanes_cache_destroy(self.handle)
+            self.handle = _P(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def neat_forward_lanes_steps(lanes, pop: int, d: Dims, inputs, outputs, cache: LanesCache, stage_bytes: int = 0,
+                             stream=None):
+    """``steps`` forwards from lane programs as one CUDA graph: inputs f32
+    [S][P][1][I] (or [S][P][I]) -> outputs f32 [S][P][1][O] (or [S][P][O])."""
+    steps = inputs.shape[0]
+    assert inputs.shape[1] == pop and outputs.shape[0] == steps and outputs.shape[1] == pop
+    assert inputs.is_contiguous() and outputs.is_contiguous()
+    _check(_lib.neat_forward_lanes_steps(_ptr(lanes), pop, d, _ptr(inputs), pop * d.num_inputs, _ptr(outputs),
+                                         pop * d.num_outputs, steps, stage_bytes, ctypes.byref(cache.handle),
+                                         _stream(stream)), "neat_forward_lanes_steps")
     return outputs
 
 

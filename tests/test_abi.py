@@ -105,3 +105,30 @@ def test_argument_errors_of_the_other_entry_points(lib_path):
     assert lib.neat_substrate_forward(16, 4, neat.Substrate(1, 3), 16, 1, 1, 1, 16, None) == neat.NEAT_EINVAL
     assert lib.neat_substrate_forward(16, 4, neat.Substrate(16, 3), 16, 1, 9, 1, 16, None) == neat.NEAT_EINVAL
     assert lib.neat_substrate_forward(None, 0, neat.Substrate(16, 3), None, 1, 1, 1, None, None) == neat.NEAT_OK
+
+
+def test_lane_program_sizes_and_argument_errors(lib_path):
+    """Lane programs: buffer sizes and the argument checks of
+    neat_lanes_pack / neat_forward_lanes, all answered on the host."""
+    from paper_2404_01817_gb300 import neat
+    lib = neat._lib
+    d = neat.dims(27, 8, 50, 200)
+    n = neat.neat_lanes_bytes(10000, d)
+    assert n > 0 and n % 128 == 0
+    assert neat.neat_lanes_bytes(10016, d) > n                     # one more warp of 16 genomes
+    assert neat.neat_lanes_bytes(0, d) > 0                         # the header
+    assert neat.neat_lanes_bytes(-1, d) == 0
+    assert neat.neat_lanes_bytes(10, neat.dims(8, 4, 129, 200)) == 0    # more than 128 nodes
+    assert neat.neat_lanes_bytes(10, neat.dims(8, 4, 128, 2000)) == 0   # a record above 12 KB
+    assert neat.neat_lanes_bytes(10, neat.dims(8, 4, 128, 1024)) > 0
+    # pack: bad dims, null pointers, alignment, a buffer too small
+    assert lib.neat_lanes_pack(16, 4, neat.dims(8, 4, 200, 400), 128, 1 << 20, None) == neat.NEAT_EINVAL
+    assert lib.neat_lanes_pack(None, 4, d, 128, 1 << 30, None) == neat.NEAT_EINVAL
+    assert lib.neat_lanes_pack(16, 4, d, 64, 1 << 30, None) == neat.NEAT_EINVAL          # not 128-byte aligned
+    assert lib.neat_lanes_pack(16, 10000, d, 128, n - 1, None) == neat.NEAT_ENOMEM
+    # forward: an empty population is a no-op; null pointers and stage sizes are checked
+    assert lib.neat_forward_lanes(None, 0, d, None, None, 0, None) == neat.NEAT_OK
+    assert lib.neat_forward_lanes(None, 4, d, 16, 16, 0, None) == neat.NEAT_EINVAL
+    assert lib.neat_forward_lanes(128, 4, d, None, 16, 0, None) == neat.NEAT_EINVAL      # I > 0 without inputs
+    assert lib.neat_forward_lanes(128, 4, neat.dims(8, 4, 129, 200), 16, 16, 0, None) == neat.NEAT_EINVAL
+    assert lib.neat_forward_lanes_steps(128, 4, d, 16, 27, 16, 8, -1, 0, None, None) == neat.NEAT_EINVAL
