@@ -4,25 +4,29 @@ tanh, sum; 1000 sequential steps with one N(0,1) observation per genome per
 step).
 
 One bench step = one episode of the hot path: transform the population once,
-then 1000 sequential forwards (Section 3.3: transform once, calculate per
-call).  Two forms are timed on the same data:
-  batched  the 1000 forwards as one CUDA graph with programmatic dependent
-           launch (neat_forward_steps) -- the headline `value`;
-  plain    one neat_forward call per step from the host.
+compile its lane programs, then 1000 sequential forwards (Section 3.3:
+transform once, calculate per call).  Two forms are timed on the same data:
+  batched  the 1000 forwards from lane programs as one CUDA graph with
+           programmatic dependent launch (neat_forward_lanes_steps) -- the
+           headline `value`;
+  plain    one neat_forward call per step from the host (one population per
+           launch, the level-walk kernel).
 `e2e` repeats the batched episode through the C ABI with the genome tensors
 and observations in pinned host memory and the actions copied back, all
 inside the timed region.
 
 The episode's observations (1.08 GB) exceed the 129 MB L2, so every episode
-streams its inputs from HBM; the transformed population (~19 MB) stays
-L2-resident across the steps of an episode, as it would between environment
-steps.
+streams its inputs from HBM; the lane programs (~13 MB) stay L2-resident
+across the steps of an episode, as they would between environment steps.
 
-`roofline` rates the forward launch by its algorithmic bytes against the
-measured HBM bandwidth; `issue_roofline` rates the same launch against the
-bound that holds it, instruction issue (warp instructions per launch, from a
-recorded ncu count for the same kernel sources, over 4 schedulers x SMs x the
-sampled SM clock).
+`roofline` rates the forward launch by the algorithmic bytes of a genome
+forward (per genome 16 B per present node and 6 B per enabled connection,
+plus 4 B per observation and per action, counted from the generated tensors)
+against the measured HBM bandwidth; the bytes the kernel actually stages
+(its lane programs) and the transformed records are reported beside it.
+`issue_roofline` rates the same launch against instruction issue.  The
+default run also measures the other four workloads (XOR latency, the uneven
+batch, the CPPN query and serving) and embeds their results under `configs`.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
        python bench.py --workload xor|batched|cppn|serving|recurrent|distance|evolve|substrate
@@ -56,6 +60,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--env-steps", type=int, default=ENV_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other four workloads in the default run")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
     ap.add_argument("--workload", choices=["ant", "xor", "batched", "cppn", "serving", "recurrent", "distance",
@@ -83,7 +88,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -131,9 +136,11 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(pop, obs_host, seconds_target=15.0):
+def cpu_baseline(pop, obs_host, seconds_target=15.0, single_seconds=5.0):
     """The FP64 oracle on the host cores over a bounded sample of the workload:
-    all genomes, the first S steps of the episode (S sized from a probe)."""
+    all genomes and the first S steps of the episode on every core (S sized
+    from a probe), and beside it the same oracle on one core over a smaller
+    sample (the first genomes, the first steps)."""
     import concurrent.futures as cf
 
     import oracle
@@ -142,7 +149,7 @@ def cpu_baseline(pop, obs_host, seconds_target=15.0):
     t0 = time.perf_counter()
     oracle.forward(pop.nodes[:200], pop.conns[:200], I, O, xs_all[:200, :50])
     per_gf = (time.perf_counter() - t0) / (200 * 50)
-    S = int(max(10, min(xs_all.shape[1], seconds_target / max(per_gf, 1e-9) / POP)))
+    S = int(max(10, min(xs_all.shape[1], seconds_target * cores / max(per_gf, 1e-9) / POP / 4)))
     chunks = np.array_split(np.arange(POP), cores * 4)
 
     def run(idx):
@@ -152,14 +159,35 @@ def cpu_baseline(pop, obs_host, seconds_target=15.0):
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
         list(ex.map(run, chunks))
     dt = time.perf_counter() - t0
+    # one core: the first G genomes x first S1 steps, about single_seconds of work
+    G = 1000
+    S1 = int(max(5, min(xs_all.shape[1], single_seconds / max(per_gf, 1e-9) / G)))
+    t0 = time.perf_counter()
+    oracle.forward(pop.nodes[:G], pop.conns[:G], I, O, xs_all[:G, :S1])
+    dt1 = time.perf_counter() - t0
     return {"value": POP * S / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"all {POP} genomes x first {S} of the episode's steps (FP64 C oracle, "
-                      f"transform once per genome + forward per step, {cores} threads)"}
+                      f"transform once per genome + forward per step, {cores} threads)",
+            "single_core": {"value": G * S1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"the first {G} genomes x first {S1} steps, one thread"}}
 
 
 WORKLOAD = ("Ant-shaped control: 10000 genomes/GPU, 27 in / 8 out, max 50 nodes / 200 conns, "
-            "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + "
-            "1000 sequential forwards (1 obs/genome/step)")
+            "0-15 hidden, 100-200 conns, 10% disabled, tanh, sum; bench step = transform + lane-program "
+            "compile + 1000 sequential forwards (1 obs/genome/step)")
+
+
+def genome_forward_bytes(pop) -> tuple[int, int, int]:
+    """Algorithmic bytes of one forward over the population: per genome 16 B
+    per present node (12 B of node parameters and 4 B of its value) and 6 B
+    per enabled connection (weight and source), plus 4 B per observation and
+    per action; returns (bytes, present nodes, enabled connections)."""
+    n = int((~np.isnan(pop.nodes[:, :, 0])).sum())
+    c = pop.conns
+    present = ~(np.isnan(c[:, :, 0]) | np.isnan(c[:, :, 1]) | np.isnan(c[:, :, 2]))
+    e = int((present & (np.nan_to_num(c[:, :, 2]) != 0)).sum())
+    P = pop.nodes.shape[0]
+    return 16 * n + 6 * e + 4 * P * (pop.num_inputs + pop.num_outputs), n, e
 
 
 def run_reference(args):
@@ -215,11 +243,17 @@ def timed_events(fn, reps, stream):
 
 
 def run_xor(args, reps=1000):
+    print(json.dumps(measure_xor(args, reps)), flush=True)
+
+
+def measure_xor(args, reps=1000):
     """XOR (100 genomes grown from the 3 -> 1 net, the 4 points with a bias
     input): latency-bound, so the line reports microseconds per call (CUDA
     events around each call, p50 / p99 over `reps` calls) for the transform
-    and the forward, and host-to-host latency of both through the public API."""
+    and the forward, and host-to-host latency of both through the public API;
+    the outputs' largest scaled error against the FP64 oracle beside it."""
     import torch
+    import oracle
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
     dev = torch.device("cuda", 0)
@@ -259,6 +293,7 @@ def run_xor(args, reps=1000):
         yh.copy_(y, non_blocking=True)
         torch.cuda.synchronize()
         host.append((time.perf_counter() - t0) * 1e6)
+    _, _, err = oracle_error(y.cpu().numpy(), oracle.forward(pop.nodes, pop.conns, 3, 1, W.xor_inputs(100)))
     line = {"metric": "XOR population latency (100 genomes x 4 inputs): microseconds per forward call (p50)",
             "value": fw[0], "unit": "us", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
             "ms_per_step": fw[0] / 1e3, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
@@ -266,16 +301,25 @@ def run_xor(args, reps=1000):
             "transform_us": {"p50": tr[0], "p99": tr[1]}, "forward_us": {"p50": fw[0], "p99": fw[1]},
             "e2e": {"value": float(np.percentile(host, 50)), "unit": "us", "p99": float(np.percentile(host, 99)),
                     "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)},
-            "clocks": clocks.summary(), "gpu_launches": 2 * reps}
-    print(json.dumps(line), flush=True)
+            "clocks": clocks.summary(), "gpu_launches": 2 * reps,
+            "parity": {"max_scaled_error": err, "compared": "all 100 genomes x 4 points vs the FP64 oracle"}}
+    return line
 
 
 def run_batched(args):
+    line = measure_batched(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batched(args):
     """Uneven batch: 4 populations x 2048 genomes (max nodes 16/64/256/1024,
     conns ~4x nodes, all activations and aggregations), 64 N(0,1) inputs per
     genome per step, 100 steps; the plan (one persistent launch per step, as
-    a CUDA graph) against plain per-population launches."""
+    a CUDA graph) against plain per-population launches; step 0's outputs of
+    16 genomes per population against the FP64 oracle."""
     import torch
+    import oracle
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
     dev = torch.device("cuda", 0)
@@ -305,6 +349,12 @@ def run_batched(args):
     for _ in range(args.warmup):
         plan.forward_steps(0, S)
     torch.cuda.synchronize()
+    errs = []
+    for j, (p, dd) in enumerate(zip(pops, descs)):
+        idx = np.arange(0, p.pop, p.pop // 16)[:16]
+        xs = dd["inputs"][0][idx].cpu().numpy()
+        ref = oracle.forward(p.nodes[idx], p.conns[idx], p.num_inputs, p.num_outputs, xs)
+        errs.append(oracle_error(dd["outputs"][0][idx].cpu().numpy(), ref)[2])
     with ClockSampler(0) as clocks:
         ms_b = timed_events(lambda: plan.forward_steps(0, S), args.steps, stream)
     launches = [neat.neat_default_launch(p.pop, dd["dims"], B) for p, dd in zip(pops, descs)]
@@ -336,14 +386,23 @@ def run_batched(args):
                          "note": "plan kernel per step; algorithmic bytes = every record once + inputs + outputs. "
                                  "The large buckets are bound by shared-memory gathers (4 B per edge per input "
                                  "vector) and FP32/SFU issue, not HBM"},
-            "gpu_launches": args.steps * S}
+            "gpu_launches": args.steps * S,
+            "parity": {"max_scaled_error": max(errs), "per_population": errs,
+                       "compared": "step 0, 16 genomes x 64 inputs per population vs the FP64 oracle"}}
     plan.close()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_cppn(args):
-    """CPPN substrate batch: 1000 CPPNs x 131072 queries (3 layers of 16x16)."""
+    print(json.dumps(measure_cppn(args)), flush=True)
+
+
+def measure_cppn(args):
+    """CPPN substrate batch: 1000 CPPNs x 131072 queries (3 layers of 16x16);
+    2000 sampled queries against the FP64 oracle (a threshold decision may
+    differ only where the raw value sits at 0.2 within the tolerance)."""
     import torch
+    import oracle
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
     dev = torch.device("cuda", 0)
@@ -362,23 +421,47 @@ def run_cppn(args):
         step()
     torch.cuda.synchronize()
     with ClockSampler(0) as clocks:
-        ms = timed_events(step, args.steps, stream)
+        ms = timed_events(step, max(args.steps, 50), stream)
+        ms_q = timed_events(lambda: neat.neat_cppn_query(rec, 1000, d, 16, 3, 0.2, w, stream=stream),
+                            max(args.steps, 50), stream)
+    rng = np.random.default_rng(9)
+    qs = np.stack([rng.integers(0, 1000, 2000), rng.integers(0, 2, 2000), rng.integers(0, 256, 2000),
+                   rng.integers(0, 256, 2000)], axis=1).astype(np.int32)
+    raw, ref = oracle.cppn_query(pop.nodes, pop.conns, 16, 0.2, qs)
+    got = w[qs[:, 0], qs[:, 1], qs[:, 2], qs[:, 3]].cpu().numpy().astype(np.float64)
+    flip = (got == 0) != (ref == 0)
+    flips_ok = bool(np.all(np.abs(np.abs(raw[flip]) - 0.2) <= 1e-5 * np.maximum(1, np.abs(raw[flip]))))
+    _, _, err = oracle_error(got[~flip], ref[~flip])
     hdr = rec.view(1000, -1)[:, :32].cpu().numpy().view(np.uint32)
     edges = hdr[:, 1].astype(np.int64)
     nonin = (hdr[:, 0] & 0xFFFF).astype(np.int64) - 5
     q = 1000 * 131072
     t = statistics.median(ms) / 1e3
+    tq = statistics.median(ms_q) / 1e3
     flops = 131072 * int((2 * edges + 2 * nonin).sum())       # one FMA per edge, bias/response FMA per node
-    sm_mhz = clocks.summary()["sm_mhz"] or 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12            # TFLOP/s at the sampled clock
+    cs = clocks.summary()
+    sm_mhz = cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s at the sampled clock
     line = {"metric": "CPPN substrate queries/s (1000 CPPNs x 131072 queries, 3 layers of 16x16)",
-            "value": q / t, "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": q / t, "unit": "queries/s", "n_gpus": 1, "steps": max(args.steps, 50), "warmup": args.warmup,
             "ms_per_step": statistics.median(ms), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": flops / t / 1e12 / fp32_peak,
-                         "note": "FMA flops of the edges and node rule only; transcendental work excluded"},
-            "clocks": clocks.summary(), "gpu_launches": 2 * args.steps}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": "CPPN", "genomes": 1000, "queries_per_genome": 131072,
+                       "l2": "no flush: 524 MB of weights written per step, larger than L2"},
+            "query_kernel_ms": tq * 1e3,
+            "roofline": {"bound": "alu", "achieved": flops / tq / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": flops / tq / 1e12 / fp32_peak,
+                         "note": f"FMA flops of the edges and node rule against {sms} SMs x 128 FP32 lanes x 2 at "
+                                 "the sampled clock; the transcendental activations (sin, exp) are not counted"},
+            "parity": {"max_scaled_error": err, "threshold_flips_at_boundary_only": flips_ok,
+                       "threshold_flips": int(flip.sum()), "compared": "2000 random queries vs the FP64 oracle"},
+            "clocks": cs, "gpu_launches": 2 * max(args.steps, 50)}
+    issue = issue_roofline_from_profile("cppn_query_traffic.json", ("neat_cppn.cu", "neat_device.cuh",
+                                                                   "neat_internal.h", "neat_item.cuh"),
+                                        tq, sms, sm_mhz)
+    if issue:
+        line["issue_roofline"] = issue
+    return line
 
 
 def run_recurrent(args, S=100, K=8):
@@ -703,69 +786,161 @@ def run_substrate(args, S=50):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, n_requests=400, n_templates=16):
-    """Serving: a Poisson stream (200 requests/s) of requests with log-uniform
-    population (64-4096), max nodes (8-512) and batch (1-256), 100 steps each,
-    through neat_serve_* at HBM budgets of 1, 4 and 16 GB.  Genomes come from
-    16 request templates drawn from that distribution (request i uses
-    template i mod 16 with its own observation seed), held in pinned memory and
-    lent to the server."""
+def run_serving(args):
+    print(json.dumps(measure_serving(args)), flush=True)
+
+
+def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
+    """Serving: a Poisson stream (200 requests/s) of `n_requests` requests,
+    each with its own log-uniform population (64-4096), max nodes (8-512)
+    and observation batch (1-256) and its own genomes (drawn per request,
+    in parallel threads ahead of the stream), 100 steps each, through
+    neat_serve_* at several HBM budgets (small ones make admission wait;
+    a request that can never fit a budget is refused and counted).  The last
+    step's outputs of three requests are checked against the FP64 oracle
+    (16 genomes each, observations regenerated with neat_fill_normal)."""
+    import collections
+    import concurrent.futures as cf
     import threading
 
     import torch
+    import oracle
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
     dev = torch.device("cuda", 0)
     reqs = W.serving_requests(0, n_requests)
-    tmpl = []
-    for k in range(n_templates):
-        r = reqs[k]
-        p = W.request_population(r)
-        nodes = torch.from_numpy(p.nodes).pin_memory()
-        conns = torch.from_numpy(p.conns).pin_memory()
-        d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
-        y = torch.empty((p.pop, r["batch"], p.num_outputs), device=dev)
-        tmpl.append(dict(r=r, nodes=nodes.numpy(), conns=conns.numpy(), keep=(nodes, conns), dims=d, y=y))
     results = {}
-    for budget_gb in (1, 4, 16):
-        srv = neat.Server(budget_gb << 30, max_active=256)
-        t = tmpl[0]
-        srv.wait(srv.submit(t["nodes"], t["conns"], t["dims"], t["r"]["batch"], 2, 1, t["y"], borrow=True))
-        srv.close()
-        srv = neat.Server(budget_gb << 30, max_active=256)
-        tickets = []
+    parity = None
+    for budget_mb in budgets_mb:
+        budget = int(budget_mb) << 20
+        srv = neat.Server(budget, max_active=256)
+        warm = W.request_population_fast(dict(reqs[0], pop=64))
+        d0 = neat.dims(warm.num_inputs, warm.num_outputs, warm.max_nodes, warm.max_conns)
+        y0 = torch.empty((64, reqs[0]["batch"], warm.num_outputs), device=dev)
+        srv.wait(srv.submit(warm.nodes, warm.conns, d0, reqs[0]["batch"], 2, 1, y0))
+        tickets, outs, refused = [], {}, []
+        lag = []
+        pool = cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1))
+        window = collections.deque()
+        ahead = 48
 
         def client():
+            nxt = 0
             t0 = time.perf_counter()
             for i, r in enumerate(reqs):
+                while nxt < len(reqs) and nxt < i + ahead:
+                    window.append(pool.submit(W.request_population_fast, reqs[nxt]))
+                    nxt += 1
+                p = window.popleft().result()
                 dt = r["arrival_s"] - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
-                t = tmpl[i % n_templates]
-                tickets.append(srv.submit(t["nodes"], t["conns"], t["dims"], t["r"]["batch"], 100, 7919 * i + 1,
-                                          t["y"], borrow=True))
+                else:
+                    lag.append(-dt)
+                d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
+                y = torch.empty((p.pop, r["batch"], p.num_outputs), device=dev)
+                try:
+                    tk = srv.submit(p.nodes, p.conns, d, r["batch"], r["steps"], r["seed"], y)
+                except neat.NeatError as e:
+                    if e.code != neat.NEAT_EBUDGET:
+                        raise
+                    refused.append(i)
+                    continue
+                tickets.append((i, tk))
+                outs[i] = (y, d)
         with ClockSampler(0) as clocks:
             th = threading.Thread(target=client)
             th.start()
             th.join()
-            for tk in tickets:
+            for i, tk in tickets:
                 srv.wait(tk, 600000)
+        pool.shutdown()
         st = srv.stats()
-        results[f"{budget_gb}GB"] = {"latency_p50_ms": st.latency_p50_ms, "latency_p99_ms": st.latency_p99_ms,
-                                     "queue_wait_p50_ms": st.queue_wait_p50_ms,
-                                     "queue_wait_p99_ms": st.queue_wait_p99_ms, "completed": st.completed,
-                                     "genome_forwards_per_s": st.genome_forwards_per_s, "ticks": st.ticks,
-                                     "clocks": clocks.summary()}
+        results[f"{budget_mb}MB"] = {
+            "latency_p50_ms": st.latency_p50_ms, "latency_p99_ms": st.latency_p99_ms,
+            "queue_wait_p50_ms": st.queue_wait_p50_ms, "queue_wait_p99_ms": st.queue_wait_p99_ms,
+            "completed": st.completed, "refused_never_fit": len(refused),
+            "genome_forwards_per_s": st.genome_forwards_per_s, "ticks": st.ticks,
+            "arrival_lag_p99_ms": float(np.percentile(lag, 99)) * 1e3 if lag else 0.0,
+            "clocks": clocks.summary()}
+        if parity is None and tickets:
+            errs = []
+            for i, _ in tickets[:3]:
+                r = reqs[i]
+                y, d = outs[i]
+                p = W.request_population_fast(r)
+                obs = torch.empty(p.pop * r["batch"] * p.num_inputs, device=dev)
+                neat.neat_fill_normal(r["seed"], r["steps"] - 1, obs)
+                x = obs.view(p.pop, r["batch"], p.num_inputs).cpu().numpy()
+                idx = np.arange(0, p.pop, max(1, p.pop // 16))[:16]
+                ref = oracle.forward(p.nodes[idx], p.conns[idx], p.num_inputs, p.num_outputs, x[idx])
+                errs.append(oracle_error(y[idx].cpu().numpy(), ref)[2])
+            parity = {"max_scaled_error": max(errs),
+                      "compared": "last step of 3 requests, 16 genomes each, vs the FP64 oracle"}
         srv.close()
-    best = results["16GB"]
+        outs.clear()
+    best = results[f"{budgets_mb[-1]}MB"]
     line = {"metric": "serving: genome-forwards/s and request latency p50/p99 ms (Poisson 200 req/s)",
             "value": best["genome_forwards_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving", "requests": n_requests, "rate_hz": 200, "steps_per_request": 100,
-                       "templates": n_templates},
+                       "genomes": "drawn per request (random_dag_population_vec, the Ant recipe at the request's "
+                                  "size)", "budgets_mb": list(budgets_mb)},
             "latency_ms": {"p50": best["latency_p50_ms"], "p99": best["latency_p99_ms"]},
-            "budgets": results}
-    print(json.dumps(line), flush=True)
+            "budgets": results, "parity": parity}
+    return line
+
+
+def oracle_error(gpu, ref):
+    """(outputs outside the tolerance, max abs error, max scaled error) of
+    float outputs against FP64 references (NaN must match NaN)."""
+    gpu = np.asarray(gpu, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    nan_ref = np.isnan(ref)
+    bad = int(np.sum(nan_ref != np.isnan(gpu)))
+    fin = ~nan_ref & np.isfinite(ref)
+    err = np.abs(gpu[fin] - ref[fin])
+    scaled = err / np.maximum(1.0, np.abs(ref[fin]))
+    bad += int(np.sum(~(scaled <= 1e-5)))
+    return bad, (float(err.max()) if err.size else 0.0), (float(scaled.max()) if err.size else 0.0)
+
+
+def issue_roofline_from_profile(fname, sources, launch_s, sms, sm_mhz):
+    """The issue roofline of a kernel from a recorded ncu instruction count
+    (profiles/<fname>, valid while its sources hash the same)."""
+    path = os.path.join(ROOT, "profiles", fname)
+    if not os.path.exists(path):
+        return None
+    try:
+        tj = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if tj.get("kernel_hash") != source_hash(sources) or not tj.get("warp_instructions_per_launch"):
+        return None
+    insts = tj["warp_instructions_per_launch"]
+    peak = 4 * sms * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": insts / launch_s, "peak": peak, "unit": "warp instructions/s",
+            "frac": insts / launch_s / peak, "instructions_per_launch": insts,
+            "note": f"ncu smsp__inst_executed.sum per launch (same sources); peak = 4 schedulers x {sms} SMs x the "
+                    "sampled SM clock"}
+
+
+def other_configs(args):
+    """The other four workloads, measured after the headline and embedded
+    in its line: XOR latency, the uneven batch, the CPPN query, serving."""
+    import torch
+    out = {}
+    small = argparse.Namespace(**vars(args))
+    small.steps = max(3, min(args.steps, 10))
+    for name, fn in (("xor", lambda: measure_xor(small, reps=1000)), ("batched", lambda: measure_batched(small)),
+                     ("cppn", lambda: measure_cppn(small)), ("serving", lambda: measure_serving(small))):
+        try:
+            out[name] = fn()
+        except Exception as e:                      # a failing workload is reported, not hidden
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -820,18 +995,23 @@ def main():
     act = torch.empty((S, POP, 1, O), device=dev)
     rec = torch.empty(neat.neat_transformed_bytes(POP, d), dtype=torch.uint8, device=dev)
     status = torch.empty(POP, dtype=torch.int32, device=dev)
+    lanes = torch.empty(neat.neat_lanes_bytes(POP, d), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    cache = neat.StepsCache()
+    cache = neat.LanesCache()
     L_plain = neat.neat_default_launch(POP, d, 1)
-    L_batched = neat.neat_default_launch(POP, d, 1)
-    L_batched.pdl = 1
-    order = torch.empty(POP, dtype=torch.int32, device=dev)
-    L_batched.order_dev = order.data_ptr()
+
+    # the lane programs' shared-memory stage: the largest warp program of this
+    # population (read once; every later pack of the same genomes gives the same)
+    neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+    neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
+    torch.cuda.synchronize(dev)
+    info = neat.neat_lanes_query(lanes)
+    stage = info.max_warp_bytes
 
     def episode_batched():
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
-        neat.neat_schedule(rec, POP, d, order, stream=stream)
-        neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
+        neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
+        neat.neat_forward_lanes_steps(lanes, POP, d, obs, act, cache, stage_bytes=stage, stream=stream)
 
     def episode_plain(step_events=None):
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
@@ -846,9 +1026,6 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
-
-    def reduce_max(x: float) -> float:
-        return max_over_ranks(x, dev)
 
     # ---- warm-up (also builds the CUDA graph)
     for _ in range(args.warmup):
@@ -869,14 +1046,14 @@ def main():
         for k in range(args.steps):
             ep_events[k][0].record(stream)
             neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
-            neat.neat_schedule(rec, POP, d, order, stream=stream)
+            neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
             fw_events[k][0].record(stream)
-            neat.neat_forward_steps(rec, POP, d, obs, act, cache, launch=L_batched, stream=stream)
+            neat.neat_forward_lanes_steps(lanes, POP, d, obs, act, cache, stage_bytes=stage, stream=stream)
             fw_events[k][1].record(stream)
             ep_events[k][1].record(stream)
         ev1.record(stream)
         barrier()
-    t_batched = reduce_max(ev0.elapsed_time(ev1) / 1e3)
+    t_batched = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev)
     ep_ms = [a.elapsed_time(b) for a, b in ep_events]
     fw_ms = [a.elapsed_time(b) for a, b in fw_events]
     value = job_throughput(POP * S * args.steps, world, t_batched)
@@ -894,7 +1071,7 @@ def main():
         step_ms += [a.elapsed_time(b) for a, b in step_ev]
     p1.record(stream)
     barrier()
-    t_plain = reduce_max(p0.elapsed_time(p1) / 1e3)
+    t_plain = max_over_ranks(p0.elapsed_time(p1) / 1e3, dev)
     value_plain = world * POP * S * n_plain / t_plain
 
     # ---- end to end through the C ABI: host genome tensors and observations
@@ -910,7 +1087,7 @@ def main():
     bounds = [0, min(S, 10)] + [b for b in range(100, S, 100) if b > min(S, 10)] + [S]
     bounds = sorted(set(bounds))
     CH = len(bounds) - 1
-    chunk_caches = [neat.StepsCache() for _ in range(CH)]
+    chunk_caches = [neat.LanesCache() for _ in range(CH)]
     copy_stream = torch.cuda.Stream(dev)
     prev_used = [None] * CH      # events: the previous episode is done with chunk c's buffers
 
@@ -921,7 +1098,7 @@ def main():
         nodes.copy_(nodes_h, non_blocking=True)
         conns.copy_(conns_h, non_blocking=True)
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
-        neat.neat_schedule(rec, POP, d, order, stream=stream)
+        neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
         with torch.cuda.stream(copy_stream):
             for c in range(CH):
                 if prev_used[c] is not None:
@@ -932,8 +1109,8 @@ def main():
         for c in range(CH):
             lo, hi = bounds[c], bounds[c + 1]
             stream.wait_event(ev_in[c])
-            neat.neat_forward_steps(rec, POP, d, obs[lo:hi], act[lo:hi], chunk_caches[c], launch=L_batched,
-                                    stream=stream)
+            neat.neat_forward_lanes_steps(lanes, POP, d, obs[lo:hi], act[lo:hi], chunk_caches[c], stage_bytes=stage,
+                                          stream=stream)
             ev_done[c].record(stream)
         with torch.cuda.stream(copy_stream):
             for c in range(CH):
@@ -957,16 +1134,17 @@ def main():
     stream.wait_event(last)                  # every action download of every episode is inside
     e1.record(stream)
     barrier()
-    t_e2e = reduce_max(e0.elapsed_time(e1) / 1e3)
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     for cc in chunk_caches:
         cc.close()
     h2d = nodes_h.numel() * 4 + conns_h.numel() * 4 + obs_h.numel() * 4
     d2h = act_h.numel() * 4
 
     # ---- roofline of the forward kernel: algorithmic bytes per launch
+    alg_bytes, n_nodes, n_edges = genome_forward_bytes(pop)
     hdr = rec.view(POP, -1)[:, :32].cpu().numpy().view(np.uint32)
-    rec_bytes = int(hdr[:, 4].astype(np.int64).sum())                    # used bytes of every record
-    alg_bytes = rec_bytes + POP * I * 4 + POP * O * 4
+    record_bytes = int(hdr[:, 4].astype(np.int64).sum())                  # used bytes of every record
+    program_bytes = lane_program_bytes(lanes, info)
     fwd_launch_s = statistics.mean(fw_ms) / 1e3 / S                      # per forward, graph-amortised
     achieved = alg_bytes / fwd_launch_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -986,10 +1164,14 @@ def main():
     # the synthetic observations do not depend on the actions, so every
     # step's inputs are known in advance and one launch runs the episode
     # with each genome's record held in shared memory
+    L_fused = neat.neat_default_launch(POP, d, 1)
+    order = neat.neat_schedule(rec, POP, d, stream=stream)
+    L_fused.order_dev = order.data_ptr()
+
     def episode_fused():
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
         neat.neat_schedule(rec, POP, d, order, stream=stream)
-        neat.neat_forward_fused(rec, POP, d, obs, act, launch=L_batched, stream=stream)
+        neat.neat_forward_fused(rec, POP, d, obs, act, launch=L_fused, stream=stream)
 
     episode_fused()
     torch.cuda.synchronize(dev)
@@ -1001,7 +1183,7 @@ def main():
         episode_fused()
     f1.record(stream)
     barrier()
-    t_fused = reduce_max(f0.elapsed_time(f1) / 1e3)
+    t_fused = max_over_ranks(f0.elapsed_time(f1) / 1e3, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1009,34 +1191,43 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "l2": "inputs larger than L2 (1.08 GB of observations per bench step)",
-                   "form": "batched: CUDA graph of the steps with programmatic dependent launch, genomes in "
-                           "depth order (neat_schedule)",
-                   "launch": {"group": L_batched.group, "tile": L_batched.tile,
-                              "groups_per_block": L_batched.groups_per_block}},
+                   "form": "batched: lane programs (neat_lanes_pack once per episode), the 1000 steps as one CUDA "
+                           "graph with programmatic dependent launch (neat_forward_lanes_steps)",
+                   "launch": {"warps": info.warps, "threads_per_block": 32, "genomes_per_warp": 16,
+                              "stage_bytes": stage}},
         "plain": {"value": value_plain, "unit": UNIT, "episodes": n_plain,
-                  "step_p50_ms": float(np.percentile(step_ms, 50)), "step_p99_ms": float(np.percentile(step_ms, 99))},
+                  "step_p50_ms": float(np.percentile(step_ms, 50)), "step_p99_ms": float(np.percentile(step_ms, 99)),
+                  "form": "one neat_forward launch per step from the host (level-walk kernel)"},
         "latency_ms": {"episode_p50": float(np.percentile(ep_ms, 50)), "episode_p99": float(np.percentile(ep_ms, 99)),
                        "step_mean_batched": statistics.mean(fw_ms) / S},
         "e2e": {"value": world * POP * S * n_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
-                "form": f"pinned host genomes and observations in, actions out, every episode; {CH} chunks "
-                        f"(the first {bounds[1]} steps, then up to 100): uploads run ahead of the graphs on a copy "
-                        "stream (a chunk's waits for the previous episode to be done with it), downloads behind"},
+                "form": f"pinned host genomes and observations in, actions out, every episode (transform, lane "
+                        f"compile, forwards); {CH} chunks (the first {bounds[1]} steps, then up to 100): uploads run "
+                        "ahead of the graphs on a copy stream (a chunk's waits for the previous episode to be done "
+                        "with it), downloads behind"},
         "fused_multistep": {"value": world * POP * S * n_fused / t_fused, "unit": UNIT, "episodes": n_fused,
                             "us_per_step": t_fused / n_fused / S * 1e6,
-                            "form": "one launch per episode (neat_forward_fused), records read once; valid only "
-                                    "because the synthetic observations ignore the actions, so not the headline"},
-        "gpu_launches": args.steps * (2 + S),
+                            "form": "one launch per episode (neat_forward_fused, level-walk kernel), records read "
+                                    "once; valid only because the synthetic observations ignore the actions, so not "
+                                    "the headline"},
+        "gpu_launches": args.steps * (4 + S),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "l2_traffic": l2_traffic,
                      "peak_kind": f"{peak_kind} hbm_gbs",
-                     "kernel": "forward_kernel (batched form, per launch, graph-amortised)",
-                     "alg_bytes_per_launch": alg_bytes},
+                     "kernel": "lanes_kernel (batched form, per launch, graph-amortised)",
+                     "alg_bytes_per_launch": alg_bytes,
+                     "alg_bytes_rule": "per genome 16 B x present nodes + 6 B x enabled connections, + 4 B x "
+                                       "(inputs + outputs); counted from the generated tensors",
+                     "present_nodes": n_nodes, "enabled_connections": n_edges,
+                     "program_bytes_per_launch": program_bytes,
+                     "record_bytes": record_bytes,
+                     "l2_traffic_over_alg": (l2_traffic / alg_bytes) if l2_traffic else None},
         "clocks": clocks.summary(),
     }
-    # the walk is bound by instruction issue, not HBM: the same launch against
-    # the SMs' issue capacity (one warp instruction per cycle per scheduler,
-    # four schedulers per SM, at the SM clock sampled during the timed region)
+    # the walk is latency-bound: the same launch against the SMs' issue
+    # capacity (one warp instruction per cycle per scheduler, four schedulers
+    # per SM, at the SM clock sampled during the timed region)
     if warp_insts:
         sm_mhz = line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz")
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -1051,19 +1242,36 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pop, obs.cpu().numpy())
     cache.close()
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["configs"] = other_configs(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def kernel_hash() -> str:
+def lane_program_bytes(lanes, info) -> int:
+    """Bytes of every warp program of a packed lanes buffer (what the forward
+    stages per launch)."""
+    raw = lanes[:256].cpu().numpy().view(np.uint64)
+    base, stride = int(raw[2]), int(raw[3])
+    total = 0
+    heads = lanes[base:base + stride * info.warps].view(info.warps, stride)[:, :16].cpu().numpy().view(np.uint32)
+    total = int(heads[:, 1].astype(np.int64).sum())
+    return total
+
+
+def source_hash(files) -> str:
     import hashlib
     h = hashlib.sha1()
-    for fn in ("neat_forward.cu", "neat_device.cuh", "neat_internal.h", "neat_item.cuh"):
+    for fn in files:
         with open(os.path.join(ROOT, "paper_2404_01817_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
+
+
+def kernel_hash() -> str:
+    return source_hash(("neat_lanes.cu", "neat_device.cuh", "neat_internal.h", "neat_item.cuh"))
 
 
 if __name__ == "__main__":

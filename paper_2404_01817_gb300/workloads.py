@@ -314,6 +314,75 @@ def request_population(req: dict) -> Population:
         acts=(ACT_TANH,), aggs=(AGG_SUM,), p_disabled=0.1, stream=6)
 
 
+def random_dag_population_vec(seed: int, pop: int, num_inputs: int, num_outputs: int,
+                              max_nodes: int, max_conns: int, hidden_max: int,
+                              edge_factors=(2, 4), p_disabled: float = 0.1,
+                              stream: int = 8) -> Population:
+    """Random feedforward genomes drawn for the whole population at once
+    (numpy array operations, no per-genome loop), for request streams that
+    need many large populations quickly.  Same recipe as
+    ``random_dag_population`` with tanh / sum and response 1: H ~ U{0..hidden_max}
+    hidden nodes, a random rank for each non-input node, E ~ U{f0 n .. f1 n}
+    connection draws (capped by Cmax and the acyclic pairs) among (lower
+    rank -> higher rank, dst non-input) pairs, repeated pairs dropped (so a
+    genome keeps slightly fewer connections than it drew), 10% disabled,
+    weights and biases N(0,1); connection rows in pair order."""
+    I, O, N, C = num_inputs, num_outputs, max_nodes, max_conns
+    rng = rng_for(seed, stream)
+    P = empty_population(pop, N, C, I, O)
+    H = rng.integers(0, max(min(hidden_max, N - I - O), 0) + 1, size=pop)
+    n = I + O + H                                   # present nodes (rows 0..n-1, key = row)
+    m = O + H                                       # non-input nodes
+    rows = np.arange(N)
+    present = rows[None, :] < n[:, None]
+    P.nodes[:, :, 0] = np.where(present, rows[None, :].astype(np.float32), np.nan)
+    P.nodes[:, :, 1] = np.where(present, rng.standard_normal((pop, N), dtype=np.float32), np.nan)
+    P.nodes[:, :, 2] = np.where(present, np.float32(1.0), np.nan)
+    P.nodes[:, :, 3] = np.where(present, np.float32(AGG_SUM), np.nan)
+    P.nodes[:, :, 4] = np.where(present, np.float32(ACT_TANH), np.nan)
+    # non-input rank r -> row: a random order of the rows I..n-1
+    key = rng.random((pop, N))
+    key[:, :I] = np.inf
+    key[~present] = np.inf
+    rank_row = np.argsort(key, axis=1)              # first m entries: the non-input rows in rank order
+    # pairs: index t over the concatenation of the per-rank source lists
+    cum = np.concatenate([[0], np.cumsum(I + np.arange(N, dtype=np.int64))])   # cum[r] = sources of ranks < r
+    total = cum[m]                                  # acyclic pairs per genome
+    E = np.minimum(rng.integers(edge_factors[0] * n, edge_factors[1] * n + 1), np.minimum(total, C))
+    # E draws with replacement per genome; repeated pairs are dropped (one
+    # sort), so a genome keeps slightly fewer than E when draws collide
+    g_of = np.repeat(np.arange(pop), E)
+    t = (rng.random(g_of.size) * total[g_of]).astype(np.int64)
+    span = int(total.max()) + 1
+    code = g_of * span + t
+    code.sort()
+    first = np.ones(code.size, dtype=bool)
+    first[1:] = code[1:] != code[:-1]
+    code = code[first]
+    g_u = code // span
+    t_u = code - g_u * span
+    start = np.searchsorted(g_u, np.arange(pop))
+    k = np.arange(g_u.size) - start[g_u]
+    dst_rank = np.searchsorted(cum, t_u, side="right") - 1
+    s = t_u - cum[dst_rank]
+    src_row = np.where(s < I, s, rank_row[g_u, np.maximum(s - I, 0)])
+    dst_row = rank_row[g_u, dst_rank]
+    P.conns[g_u, k, 0] = src_row
+    P.conns[g_u, k, 1] = dst_row
+    P.conns[g_u, k, 2] = (rng.random(g_u.size) >= p_disabled).astype(np.float32)
+    P.conns[g_u, k, 3] = rng.standard_normal(g_u.size, dtype=np.float32)
+    return P
+
+
+def request_population_fast(req: dict) -> Population:
+    """Genomes of one serving request drawn with ``random_dag_population_vec``:
+    the Ant recipe at the request's size (hidden nodes up to capacity,
+    2n..4n connections)."""
+    I, O, nmax = req["num_inputs"], req["num_outputs"], req["max_nodes"]
+    return random_dag_population_vec(req["seed"], req["pop"], I, O, nmax, req["max_conns"],
+                                     hidden_max=max(nmax - I - O, 0), edge_factors=(2, 4))
+
+
 def random_recurrent_population(seed: int, pop: int, num_inputs: int, num_outputs: int,
                                 max_nodes: int, max_conns: int,
                                 hidden: Callable[[np.random.Generator], int],
