@@ -118,12 +118,8 @@ bool lanes_dims_ok(const neat_dims &d)
            record_max_bytes(d.num_inputs, d.num_outputs, d.max_nodes, d.max_conns) <= kLaneMaxRecord;
 }
 
-// Copy `bytes` (a multiple of 16) from global to shared memory with the 32
-// lanes of a warp.
-__device__ __forceinline__ void warp_copy16(uint4 *dst, const uint4 *__restrict__ src, uint32_t bytes, int lane)
-{
-    for (uint32_t i = (uint32_t)lane; i < bytes / 16u; i += 32u) dst[i] = __ldg(src + i);
-}
+// Library error word of the lane-program kernels: a bounded wait expired.
+__device__ unsigned int g_lanes_error;
 
 // ------------------------------------------------------------- scheduling
 
@@ -136,6 +132,13 @@ __device__ __forceinline__ void warp_copy16(uint4 *dst, const uint4 *__restrict_
 // also writes the buffer header (its reductions zero).
 constexpr int kSchedWarps = 4;
 
+// Shared memory of the schedule kernel per warp: the record, heights,
+// schedule positions and the genome's scratch image; mbarriers first.
+__host__ __device__ inline uint32_t sched_warp_bytes(uint32_t rec_bytes, int N, uint32_t scr_stride)
+{
+    return rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N) + scr_stride;
+}
+
 __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uint8_t *rec, size_t stride, int pop,
                                                                       int I, int O, int N, uint32_t rec_bytes,
                                                                       uint8_t *lanes, LanesGeom geo,
@@ -143,15 +146,17 @@ __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uin
 {
     uint8_t *sm = lane_sm;
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t per_warp = rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N);
-    uint8_t *srec = sm + (size_t)wi * per_warp;
+    const uint32_t per_warp = sched_warp_bytes(rec_bytes, N, (uint32_t)geo.scr_stride);
+    uint8_t *srec = sm + 128 + (size_t)wi * per_warp;
     uint32_t *hgt = reinterpret_cast<uint32_t *>(srec + rec_bytes);
     uint8_t *sbv = reinterpret_cast<uint8_t *>(hgt + N);
+    uint8_t *scr = srec + rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N);   // the scratch image
+    const uint32_t bar = smem_addr(sm) + 8u * (uint32_t)wi;
     if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<LanesHeader *>(lanes) = hv;
     const int g = blockIdx.x * kSchedWarps + wi;
     if (g >= pop) return;
     const uint8_t *grec = rec + (size_t)g * stride;
-    uint8_t *scr = lanes + geo.scr_off + (size_t)g * geo.scr_stride;
+    uint8_t *gscr = lanes + geo.scr_off + (size_t)g * geo.scr_stride;
     uint8_t *sched = scr + 16;
     uint8_t *vslot = sched + N * kLaneG;
     uint32_t *meas = reinterpret_cast<uint32_t *>(lanes + geo.meas_off);
@@ -159,13 +164,27 @@ __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uin
     if (h0.z & NEAT_G_ERROR_MASK) {
         if (lane == 0) {
             meas[g] = kMeasError << 24;
-            reinterpret_cast<uint4 *>(scr)[0] = make_uint4(0u, kMeasError, 0u, 0u);
+            reinterpret_cast<uint4 *>(gscr)[0] = make_uint4(0u, kMeasError, 0u, 0u);
         }
         return;
     }
+    // the record into shared memory: one bulk copy, bounded wait
     const uint32_t used = min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)), rec_bytes);
-    warp_copy16(reinterpret_cast<uint4 *>(srec), reinterpret_cast<const uint4 *>(grec), used, lane);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, used);
+        bulk_g2s(smem_addr(srec), grec, used, bar);
+    }
     __syncwarp();
+    if (!__all_sync(0xffffffffu, mbar_wait(bar, 0))) {
+        if (lane == 0) {
+            atomicOr(&g_lanes_error, kErrWaitExpired);
+            meas[g] = kMeasUnordered << 24;          // never scheduled: NaN outputs
+            reinterpret_cast<uint4 *>(gscr)[0] = make_uint4(0u, kMeasUnordered, 0u, 0u);
+        }
+        mbar_wait(bar, 0);                           // the copy lands before the block's memory is reused
+        return;
+    }
     const uint4 h1 = reinterpret_cast<const uint4 *>(srec)[1];
     const int n = (int)(h0.x & 0xffffu), nl = (int)(h0.x >> 16);
     const uint4 *nodes = reinterpret_cast<const uint4 *>(srec + kHeaderBytes);
@@ -287,6 +306,9 @@ __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uin
         uint4 head = make_uint4(nb, flags, lane_quads[0], kLaneG > 1 ? lane_quads[1] : 0u);
         reinterpret_cast<uint4 *>(scr)[0] = head;
     }
+    __syncwarp();
+    for (uint32_t i = (uint32_t)lane; i < (uint32_t)geo.scr_stride / 16u; i += 32u)
+        reinterpret_cast<uint4 *>(gscr)[i] = reinterpret_cast<const uint4 *>(scr)[i];
 }
 
 // One stable counting pass over 128 buckets by one block of 1024 threads:
@@ -376,29 +398,40 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
     const uint32_t per = rec_bytes + (uint32_t)geo.scr_stride;
     LanesHeader *hdr = reinterpret_cast<LanesHeader *>(lanes);
     const int32_t *order = reinterpret_cast<const int32_t *>(lanes + geo.ord_a_off);
-    // stage the kLaneJ genomes' schedules and records
-    for (int jj = 0; jj < kLaneJ; ++jj) {
-        const int kk = w * kLaneJ + jj;
-        if (kk >= pop) break;
-        const int gg = order[kk];
-        uint8_t *dst = sm + (size_t)jj * per;
-        const uint8_t *scr = lanes + geo.scr_off + (size_t)gg * geo.scr_stride;
-        warp_copy16(reinterpret_cast<uint4 *>(dst + rec_bytes), reinterpret_cast<const uint4 *>(scr),
-                    (uint32_t)geo.scr_stride, lane);
-        const uint8_t *grec = rec + (size_t)gg * stride;
-        const uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(grec));
-        const uint32_t used = (h0.z & NEAT_G_ERROR_MASK) ? 32u
-                              : min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)), rec_bytes);
-        warp_copy16(reinterpret_cast<uint4 *>(dst), reinterpret_cast<const uint4 *>(grec), used, lane);
-    }
+    // stage the kLaneJ genomes' schedules and records: lane jj issues the two
+    // bulk copies of genome jj, all on one mbarrier (bounded wait)
+    const uint32_t bar = smem_addr(lane_sm);
+    uint8_t *stage = sm + 128;
+    if (lane == 0) mbar_init(bar, 32);
     __syncwarp();
+    {
+        const int kk = w * kLaneJ + lane;
+        if (lane < kLaneJ && kk < pop) {
+            const int gg = order[kk];
+            uint8_t *dst = stage + (size_t)lane * per;
+            const uint8_t *gscr = lanes + geo.scr_off + (size_t)gg * geo.scr_stride;
+            const uint8_t *grec = rec + (size_t)gg * stride;
+            const uint32_t used = min(align16(__ldg(reinterpret_cast<const uint32_t *>(grec) + 4)), rec_bytes);
+            mbar_arrive_expect_tx(bar, used + (uint32_t)geo.scr_stride);
+            bulk_g2s(smem_addr(dst), grec, used, bar);
+            bulk_g2s(smem_addr(dst + rec_bytes), gscr, (uint32_t)geo.scr_stride, bar);
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+        }
+    }
+    const bool staged_ok = __all_sync(0xffffffffu, mbar_wait(bar, 0));
+    if (!staged_ok) {
+        if (lane == 0) atomicOr(&g_lanes_error, kErrWaitExpired);
+        mbar_wait(bar, 0);                 // the copies land before shared memory is read or released
+    }
     const int kg = w * kLaneJ + j;
     const int g = kg < pop ? order[kg] : -1;
-    const uint8_t *srec = sm + (size_t)j * per;
+    const uint8_t *srec = stage + (size_t)j * per;
     const uint8_t *scr = srec + rec_bytes;
     const uint4 sh = reinterpret_cast<const uint4 *>(scr)[0];
     uint32_t flags = 0;
     if (g >= 0) flags = (sh.y & kMeasError) ? kLaneError : ((sh.y & kMeasUnordered) ? kLaneUnordered : 0u);
+    if (g >= 0 && !staged_ok) flags = kLaneError;     // nothing staged can be trusted: NaN outputs
     const bool ok = g >= 0 && flags == 0;
     const int nb = ok ? (int)sh.x : 0;
     const int my_quads = ok ? (int)(k == 0 ? sh.z : sh.w) : 0;
@@ -498,8 +531,6 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
 }
 
 // ---------------------------------------------------------------- forward
-
-__device__ unsigned int g_lanes_error;
 
 struct LanesArgs {
     const uint8_t *lanes;
@@ -900,11 +931,11 @@ extern "C" int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_di
     const uint8_t *rec = static_cast<const uint8_t *>(transformed_dev);
     const size_t stride = record_stride(d);
     const int N = d.max_nodes;
-    const size_t sched_smem = (size_t)kSchedWarps * (g.rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N));
+    const size_t sched_smem = 128u + (size_t)kSchedWarps * sched_warp_bytes(g.rec_bytes, N, (uint32_t)g.scr_stride);
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(lanes_sched_kernel), sched_smem,
                                 "neat_lanes_pack: shared memory");
     if (rc) return rc;
-    const size_t pack_smem = (size_t)kLaneJ * (g.rec_bytes + g.scr_stride);
+    const size_t pack_smem = 128u + (size_t)kLaneJ * (g.rec_bytes + g.scr_stride);
     rc = allow_dynamic_smem(reinterpret_cast<const void *>(lanes_pack_kernel), pack_smem,
                             "neat_lanes_pack: shared memory");
     if (rc) return rc;
