@@ -641,12 +641,16 @@ NEAT_API void neat_plan_destroy(neat_plan *plan);
  * Inputs and outputs are the caller's, as in neat_pop_desc; step s reads
  * inputs_dev + s * in_step_stride and writes outputs_dev + s * out_step_stride.
  * The first call on a device, with that device current, looks up the array's
- * device address and fills its index list (a small kernel on `stream`); make
- * that first call before any stream capture.  Every call shares the array and
+ * device address and fills its index list (a small kernel on `stream`, which
+ * that call waits for before returning); make that first call before any
+ * stream capture.  Each call writes its bucket table into the array with one
+ * small kernel (the table is a kernel argument; nothing is copied from host
+ * memory), then launches the persistent kernel.  Every call shares the array and
  * rewrites it: calls that overlap on the GPU (other streams, other threads)
  * race, so serialise them.  Results equal neat_forward on each population.
  * Errors: NEAT_EINVAL (more than 64 populations, more than 32768 genomes in
- * one, a genome too large for one block, bad arguments), NEAT_ECUDA.
+ * one, a genome too large for one block, more than 2^31 - 1 block work
+ * items, bad arguments), NEAT_ECUDA.
  */
 NEAT_API int neat_forward_multi_noalloc(const neat_pop_desc *pops_host, int32_t npops, int32_t step, void *stream);
 

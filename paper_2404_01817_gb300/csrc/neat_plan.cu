@@ -15,6 +15,7 @@
 // mbarrier) and then runs the same item evaluation as the single-population
 // kernel (run_item), so results match neat_forward bit for bit.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -776,6 +777,23 @@ __global__ void noalloc_fill_indices(int32_t *idx, int n)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
 }
 
+// The call's bucket table travels as a kernel argument (no host-to-device
+// copy); one small kernel writes it into the scratch array and clears the
+// work counter.
+struct NoallocTable {
+    BucketDev b[kNoallocMaxPops];
+};
+
+__global__ void noalloc_set_table(const NoallocTable t, int nb, BucketDev *dst, unsigned int *counter)
+{
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(t.b);
+    uint32_t *out = reinterpret_cast<uint32_t *>(dst);
+    const int words = nb * (int)(sizeof(BucketDev) / sizeof(uint32_t));
+    for (int i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+    if (threadIdx.x == 0) *counter = 0u;
+}
+static_assert(sizeof(BucketDev) % sizeof(uint32_t) == 0, "bucket entries copy as words");
+
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_base[256] = {};   // device address of the scratch array, per device id
 
@@ -798,6 +816,10 @@ int noalloc_setup(cudaStream_t s, unsigned char **base)
     noalloc_fill_indices<<<64, 256, 0, s>>>(reinterpret_cast<int32_t *>(static_cast<unsigned char *>(p) + kNoallocIdxOff),
                                             kNoallocMaxGenomes);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: index fill");
+    // the index list is complete before any call (on any stream or thread)
+    // can see the cached address
+    e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: index fill");
     g_noalloc_base[dev] = static_cast<unsigned char *>(p);
     *base = g_noalloc_base[dev];
@@ -834,7 +856,8 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
 
     // one bucket per population, shapes from the heuristic, reserved record size
     const int NT = 256;
-    BucketDev table[kNoallocMaxPops];
+    NoallocTable tab;
+    BucketDev *table = tab.b;
     int order[kNoallocMaxPops];
     int nb = 0;
     for (int p = 0; p < npops; ++p)
@@ -848,7 +871,7 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
             std::swap(order[j], order[j - 1]);
         }
     size_t smem_regions = 0;
-    int cta = 0;
+    int64_t cta = 0;
     for (int i = 0; i < nb; ++i) {
         const neat_pop_desc &pd = pops[order[i]];
         const Shape sh = heuristic_shape(pd.dims.max_nodes, pd.batch, NT);
@@ -882,9 +905,12 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
         d.region_words = (int)(reg / 16);
         d.rec_words = (int)(rec / 16);
         d.rec_copy_bytes = (int)rec;
-        d.cta_begin = cta;
-        d.cta_items = (int)(((long)d.n_genomes * d.tiles + gpc - 1) / gpc);
-        cta += d.cta_items;
+        const int64_t items = ((int64_t)d.n_genomes * d.tiles + gpc - 1) / gpc;
+        if (items > INT_MAX || cta + items > INT_MAX)
+            return invalid("neat_forward_multi_noalloc: more than 2^31 - 1 block work items in one call");
+        d.cta_begin = (int)cta;
+        d.cta_items = (int)items;
+        cta += items;
         smem_regions = std::max(smem_regions, reg * gpc);
     }
     if (nb == 0) return NEAT_OK;
@@ -899,18 +925,19 @@ extern "C" int neat_forward_multi_noalloc(const neat_pop_desc *pops, int32_t npo
                                           "neat_forward_multi_noalloc: shared memory per block");
         if (rc) return rc;
     }
-    e = cudaMemsetAsync(base, 0, sizeof(unsigned int), s);               // the work counter starts at zero
-    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: counter reset");
-    e = cudaMemcpyAsync(base + kNoallocTableOff, table, sizeof(BucketDev) * (size_t)nb, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: table copy");
+    // the bucket table and a zero work counter, by one small kernel
+    noalloc_set_table<<<1, 256, 0, s>>>(tab, nb, reinterpret_cast<BucketDev *>(base + kNoallocTableOff),
+                                        reinterpret_cast<unsigned int *>(base));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: table");
     int dev = 0, sms = 152, smem_sm = 233472;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     int per_sm = std::max(1, std::min((int)(smem_sm / (smem + 1024)), 2048 / NT));
-    const int grid = std::max(1, std::min(sms * per_sm, cta));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, cta));
     plan_kernel<false><<<grid, NT, smem, s>>>(reinterpret_cast<const BucketDev *>(base + kNoallocTableOff), nb, 0,
-                                              cta, reinterpret_cast<unsigned int *>(base), step);
+                                              (int)cta, reinterpret_cast<unsigned int *>(base), step);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_forward_multi_noalloc: launch");
     return NEAT_OK;
