@@ -15,7 +15,9 @@ every iteration, the size FP32 rounding injects); an output passes within
 1e-5 max(1, |ref|) + 64 s, and at least 99% of outputs must meet the plain
 bound.  Bounded activations run up to K = 25; populations with every
 activation and aggregation (identity, relu and product also grow in
-magnitude around a cycle) run at K <= 3.
+magnitude around a cycle) run up to K = 8, within the plain tolerance up to
+K = 3.  Each comparison prints a RECURRENT-PARITY line with its largest
+scaled error and the number of outputs that needed the sensitivity term.
 """
 import numpy as np
 import pytest
@@ -73,7 +75,12 @@ def _bias_sensitivity(nodes, conns, I, O, x, K, ref):
 
 
 def _assert_close_conditioned(y, ref, nodes, conns, I, O, x, K, what):
-    bad_plain, _, _, n = compare_outputs(y, ref)
+    """The conditioned tolerance; prints one record line per call (largest
+    scaled error, outputs that needed the sensitivity term) so that the
+    relaxation's use is visible in every run."""
+    bad_plain, mabs, mscaled, n = compare_outputs(y, ref)
+    print(f"RECURRENT-PARITY {what}: K={K} max_scaled={mscaled:.3g} max_abs={mabs:.3g} "
+          f"needed_sensitivity_term={bad_plain} of {n}")
     assert bad_plain <= 0.01 * n, f"{what}: {bad_plain} of {n} outputs outside the plain tolerance"
     if bad_plain:
         s = _bias_sensitivity(nodes, conns, I, O, x, K, ref)
@@ -139,14 +146,16 @@ def test_recurrent_matches_oracle_bounded(neat, batch, K):
         assert (y == 0).all()                            # no iteration: every non-input node is still 0
 
 
-@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 8])
 def test_recurrent_all_activations_and_aggregations(neat, K):
     pop = _population(200 + K, pop=211, acts=W.ALL_ACTS, aggs=W.ALL_AGGS)
     x = W.normal_inputs(300 + K, (pop.pop, 5, 4))
     _, st, y = _run(neat, pop.nodes, pop.conns, 4, 3, x, K)
     ref, ref_st = oracle.forward_recurrent(pop.nodes, pop.conns, 4, 3, x, K)
     np.testing.assert_array_equal(st, ref_st)
-    assert_outputs_close(y, ref, what=f"recurrent all acts/aggs K {K}")
+    if K <= 3:
+        assert_outputs_close(y, ref, what=f"recurrent all acts/aggs K {K}")
+    _assert_close_conditioned(y, ref, pop.nodes, pop.conns, 4, 3, x, K, "all activations and aggregations")
 
 
 @pytest.mark.parametrize("batch", [1, 6])

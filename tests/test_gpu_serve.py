@@ -68,7 +68,9 @@ def test_serve_matches_direct_and_oracle(neat):
 
 
 def test_serve_alone_equals_mixed(neat):
-    """A request's outputs are bit-identical alone and among other requests."""
+    """A request's outputs are bit-identical alone and among other requests
+    whose work is on the device at the same time (their admit..done
+    intervals overlap the request's)."""
     req, p = _request(2, 257, 50, 3)
     srv = neat.Server(1 << 30)
     t, y_alone = _submit(neat, srv, req, p)
@@ -76,12 +78,19 @@ def test_serve_alone_equals_mixed(neat):
     srv.close()
     srv = neat.Server(1 << 30, max_active=16)
     others = [_request(10 + k, 64 + 97 * k, [8, 30, 120, 300, 16][k % 5], [1, 5, 17, 2, 64][k % 5]) for k in range(8)]
+    others = [(dict(r, steps=50), q) for r, q in others]       # long enough to run beside the request
     tickets = [_submit(neat, srv, r, q) for r, q in others[:4]]
     t, y_mixed = _submit(neat, srv, req, p)
     tickets += [_submit(neat, srv, r, q) for r, q in others[4:]]
-    assert srv.wait(t)[0] == neat.NEAT_OK
+    code, res = srv.wait(t)
+    assert code == neat.NEAT_OK
+    spans = []
     for tk, _ in tickets:
-        assert srv.wait(tk)[0] == neat.NEAT_OK
+        c, r = srv.wait(tk)
+        assert c == neat.NEAT_OK
+        spans.append((r.admit_ms, r.done_ms))
+    overlapping = sum(1 for a, b in spans if a < res.done_ms and b > res.admit_ms)
+    assert overlapping >= 2, f"only {overlapping} requests were active beside the request"
     np.testing.assert_array_equal(y_alone.cpu().numpy(), y_mixed.cpu().numpy())
     for (r, q), (tk, y) in zip(others, tickets):
         direct, _ = _direct(neat, q, r["batch"], r["steps"], r["seed"])
@@ -111,11 +120,17 @@ def test_serve_budget_queueing_cancel_and_timeouts(neat):
     assert r2.admit_ms >= r1.done_ms - 1e-6
     assert c3 == neat.NEAT_ECANCELLED
     np.testing.assert_array_equal(y1.cpu().numpy(), y2.cpu().numpy())
-    # a bounded host wait on an unfinished request returns NEAT_ETIMEOUT
-    t4, _ = _submit(neat, srv, dict(req, steps=2000), p)
-    code, _ = srv.wait(t4, 0)
-    assert code in (neat.NEAT_ETIMEOUT, neat.NEAT_OK)
-    assert srv.poll(t4)[0] in (neat.NEAT_EAGAIN, neat.NEAT_OK)
+    # a bounded host wait on a request that cannot be done yet (20 000 steps,
+    # each at least one kernel launch) expires with NEAT_ETIMEOUT; cancelling
+    # it then stops it
+    import torch
+    d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
+    y4 = torch.empty((p.pop, req["batch"], p.num_outputs), device="cuda")     # every step overwrites it
+    t4 = srv.submit(p.nodes, p.conns, d, req["batch"], 20000, req["seed"], y4)
+    code, _ = srv.wait(t4, 1)
+    assert code == neat.NEAT_ETIMEOUT
+    assert srv.poll(t4)[0] == neat.NEAT_EAGAIN
     srv.cancel(t4)
-    assert srv.wait(t4)[0] in (neat.NEAT_ECANCELLED, neat.NEAT_OK)
+    code, r4 = srv.wait(t4, 60000)
+    assert code == neat.NEAT_ECANCELLED and r4.genome_forwards < 400 * 4 * 20000
     srv.close()

@@ -393,6 +393,13 @@ def _status(nodes_rows, conns_rows, I=2, O=1):
     ("dangling", BASE_NODES, BASE_CONNS + [(7, 2, 1, 1.0)], DANGLING),
     ("dangling_disabled_silent", BASE_NODES, BASE_CONNS + [(7, 2, 0, 1.0)], 0),
     ("into_input", BASE_NODES, BASE_CONNS + [(3, 0, 1, 1.0)], INTO_INPUT),
+    # a duplicated key: one row stands for the key in every lookup (the
+    # lowest), so the other checks still run and add their bits
+    ("dup_key_dangling", BASE_NODES + [(3, 0, 1, 0, 1)], BASE_CONNS + [(3, 7, 1, 1.0)], DUPKEY | DANGLING),
+    ("dup_key_valid_edges", BASE_NODES + [(3, 0, 1, 0, 1)], BASE_CONNS + [(2, 3, 0, 1.0)], DUPKEY),
+    ("dup_key_cycle", BASE_NODES + [(3, 0, 1, 0, 1)], BASE_CONNS + [(2, 3, 1, 1.0)], DUPKEY | CYCLE),
+    ("dup_key_higher_row_first", [(3, 0, 1, 0, 1)] + BASE_NODES, BASE_CONNS + [(2, 3, 1, 1.0)], DUPKEY | CYCLE),
+    ("dup_input_key", BASE_NODES + [(0, 0, 1, 0, 0)], BASE_CONNS + [(3, 0, 1, 1.0)], DUPKEY | INTO_INPUT),
 ])
 def test_status_bits(name, nodes_rows, conns_rows, want):
     st, y = _status(nodes_rows, conns_rows)
