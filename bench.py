@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other four workloads in the default run")
     ap.add_argument("--profile", action="store_true",
-                    help="short case for ncu: transform, 3 plain forwards, one 8-step graph; no timing")
+                    help="short case for ncu (ant: transform, lane compile, 4 forwards, an 8-step graph; "
+                         "batched: one plan step); no timing")
     ap.add_argument("--workload", choices=["ant", "xor", "batched", "cppn", "serving", "recurrent", "distance",
                                            "evolve", "substrate"],
                     default="ant", help="ant: the headline line; the others: the other shapes")
@@ -503,7 +504,7 @@ def run_recurrent(args, S=100, K=8):
     torch.cuda.synchronize()
     assert torch.equal(y, y_eager), "graph replay differs from eager launches"
     with ClockSampler(0) as clocks:
-        ms = timed_events(graph.replay, args.steps, stream)
+        ms = timed_events(graph.replay, max(args.steps, 50), stream)
     t_step = statistics.median(ms) / 1e3 / S
     hdr = rec.view(POP, -1)[:, :32].cpu().numpy().view(np.uint32)
     used = int(hdr[:, 4].astype(np.int64).sum())
@@ -517,6 +518,13 @@ def run_recurrent(args, S=100, K=8):
     t0 = time.perf_counter()
     oracle.forward_recurrent(sub.nodes, sub.conns, I, O, xs, K)
     dt = time.perf_counter() - t0
+    dt_all, cores = oracle_cores(lambda c: oracle.forward_recurrent(sub.nodes[c], sub.conns[c], I, O, xs[c], K),
+                                 idx.size)
+    cs = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue = issue_roofline_from_profile("recurrent_ant_traffic.json", ("neat_recurrent.cu", "neat_device.cuh",
+                                                                      "neat_internal.h", "neat_item.cuh"),
+                                        t_step, sms, cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0)
     line = {"metric": f"recurrent genome-forwards/s (10000 Ant-shaped recurrent genomes, K={K} iterations, B=1)",
             "value": POP / t_step, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_step * 1e3, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -530,9 +538,12 @@ def run_recurrent(args, S=100, K=8):
                          "note": "algorithmic bytes = used record bytes + observations + actions per step; the "
                                  "kernel makes K passes over the staged edges per byte read, so it is bound by "
                                  "instruction issue (divergent per-node edge loops), not by HBM"},
-            "cpu_baseline": {"value": idx.size * 10 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{idx.size} genomes x 10 steps, FP64 C oracle, one thread"},
-            "clocks": clocks.summary(), "gpu_launches": args.steps * S}
+            "cpu_baseline": {"value": idx.size * 10 / dt_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{idx.size} genomes x 10 steps, FP64 C oracle, {cores} threads",
+                             "single_core": {"value": idx.size * 10 / dt, "unit": UNIT, "cores": 1}},
+            "clocks": cs, "gpu_launches": max(args.steps, 50) * S}
+    if issue:
+        line["issue_roofline"] = issue
     print(json.dumps(line), flush=True)
 
 
@@ -578,8 +589,9 @@ def run_distance(args, R=64):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    n_rep = max(args.steps, 300)
     with ClockSampler(0) as clocks:
-        ms = timed_events(step, args.steps, stream)
+        ms = timed_events(step, n_rep, stream)
     parts = []
     for _ in range(5):
         step(record=True)
@@ -599,6 +611,13 @@ def run_distance(args, R=64):
     t0 = time.perf_counter()
     oracle.distance(pop.nodes[idx], pop.conns[idx], pop.nodes[reps], pop.conns[reps], 1.0, 0.5)
     dt = time.perf_counter() - t0
+    dt_all, cores = oracle_cores(lambda c: oracle.distance(pop.nodes[idx[c]], pop.conns[idx[c]], pop.nodes[reps],
+                                                           pop.conns[reps], 1.0, 0.5), idx.size)
+    cs = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue = issue_roofline_from_profile("distance_traffic.json", ("neat_distance.cu", "neat_device.cuh",
+                                                                 "neat_internal.h"),
+                                        dist_ms / 1e3, sms, cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0)
     line = {"metric": "genome-pair distances/s (10000 Ant-shaped genomes x 64 representatives, with gene records "
                       "and species assignment)",
             "value": POP * R / t, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -612,10 +631,13 @@ def run_distance(args, R=64):
                          "note": "distance kernel; algorithmic bytes = used gene-record bytes of both sides + the "
                                  "f32 distance matrix; the kernel is bound by instruction issue (hash lookups "
                                  "in shared memory and warp reductions), not by HBM"},
-            "cpu_baseline": {"value": idx.size * R / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": idx.size * R / dt_all, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": f"{idx.size} genomes x {R} representatives, FP64 C oracle (all-pairs "
-                                       f"gene matching), one thread"},
-            "clocks": clocks.summary(), "gpu_launches": 4 * args.steps}
+                                       f"gene matching), {cores} threads",
+                             "single_core": {"value": idx.size * R / dt, "unit": "pairs/s", "cores": 1}},
+            "clocks": cs, "gpu_launches": 4 * n_rep}
+    if issue:
+        line["issue_roofline"] = issue
     print(json.dumps(line), flush=True)
 
 
@@ -676,8 +698,9 @@ def run_evolve(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    n_rep = max(args.steps, 400)
     with ClockSampler(0) as clocks:
-        ms = timed_events(step, args.steps, stream)
+        ms = timed_events(step, n_rep, stream)
     parts = []
     for _ in range(5):
         step(record=True)
@@ -705,6 +728,19 @@ def run_evolve(args):
                                                        weight_replace_rate=0.1),
                   mw, zz, np.arange(idx.size) + 1000)
     dt = time.perf_counter() - t0
+    mcfg = oracle.mutation_config(node_add=0.2, conn_add=0.4, bias_init_std=1.0, bias_mutate_power=0.5,
+                                  bias_mutate_rate=0.7, bias_replace_rate=0.1, weight_init_std=1.0,
+                                  weight_mutate_power=0.5, weight_mutate_rate=0.8, weight_replace_rate=0.1)
+
+    def vary(c):
+        cn_c, cc_c = oracle.crossover(pop.nodes, pop.conns, parents_h[idx[c]], xw[c])
+        oracle.mutate(cn_c, cc_c, I, O, mcfg, mw[c], zz[c], c + 1000)
+    dt_all, cores = oracle_cores(vary, idx.size)
+    cs = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue = issue_roofline_from_profile("mutate_traffic.json", ("neat_evolve.cu", "neat_device.cuh",
+                                                               "neat_internal.h", "neat_hash.cuh"),
+                                        comp["mutate"] / 1e3, sms, cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0)
     line = {"metric": "genomes/s through one generation of variation (10000 Ant-shaped genomes: random inputs, "
                       "crossover, mutation, transform)",
             "value": POP / t, "unit": "genomes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -717,10 +753,13 @@ def run_evolve(args):
                          "note": "mutation kernel: child tensors read + written and its random inputs read; "
                                  "one block per genome runs the structural steps with block barriers, so it is "
                                  "latency-bound"},
-            "cpu_baseline": {"value": idx.size / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{idx.size} children: crossover + mutation, FP64 C oracle, one thread "
-                                       f"(transform not included)"},
-            "clocks": clocks.summary(), "gpu_launches": 6 * args.steps}
+            "cpu_baseline": {"value": idx.size / dt_all, "unit": "genomes/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{idx.size} children: crossover + mutation, FP64 C oracle, {cores} threads "
+                                       f"(transform not included)",
+                             "single_core": {"value": idx.size / dt, "unit": "genomes/s", "cores": 1}},
+            "clocks": cs, "gpu_launches": 6 * n_rep}
+    if issue:
+        line["issue_roofline"] = issue
     print(json.dumps(line), flush=True)
 
 
@@ -891,6 +930,19 @@ def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
     return line
 
 
+def oracle_cores(fn, n_items, chunks_per_core=4):
+    """Time fn(idx) over all host cores (threads; the oracle releases the GIL
+    inside its C calls) on index chunks covering range(n_items); returns
+    (seconds, cores)."""
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 1
+    chunks = [c for c in np.array_split(np.arange(n_items), cores * chunks_per_core) if c.size]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(fn, chunks))
+    return time.perf_counter() - t0, cores
+
+
 def oracle_error(gpu, ref):
     """(outputs outside the tolerance, max abs error, max scaled error) of
     float outputs against FP64 references (NaN must match NaN)."""
@@ -984,6 +1036,9 @@ def main():
     from paper_2404_01817_gb300 import workloads as W
 
     S = args.env_steps
+    if args.profile:
+        profile_ant(args, dev)
+        return
     from paper_2404_01817_gb300.shard import job_throughput, max_over_ranks, population_seed
     pop = W.ant_population(population_seed(rank), POP)     # each rank evaluates its own population
     d = neat.dims(I, O, NMAX, CMAX)
@@ -1149,7 +1204,7 @@ def main():
     achieved = alg_bytes / fwd_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = l2_traffic = warp_insts = None
-    prof = os.path.join(ROOT, "profiles", "forward_ant_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "lanes_ant_traffic.json")
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
@@ -1248,6 +1303,37 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def profile_ant(args, dev):
+    """A short Ant case for ncu: transform, lane-program compile, four single
+    lane forwards, then an 8-step lane graph (no timing).  Launch order:
+    transform, the three compile kernels, lanes_kernel x 4, then the graph's
+    eight lanes_kernel launches."""
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    pop = W.ant_population(0, POP)
+    d = neat.dims(I, O, NMAX, CMAX)
+    rec, st = neat.neat_transform(torch.from_numpy(pop.nodes).to(dev), torch.from_numpy(pop.conns).to(dev), d)
+    lanes = neat.neat_lanes_pack(rec, POP, d)
+    torch.cuda.synchronize(dev)
+    info = neat.neat_lanes_query(lanes)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    # 160 steps of observations (173 MB, more than L2) drawn in order: the
+    # first 8, used below, have left L2 again, so the forwards read their
+    # inputs from HBM as in the timed episode
+    x = torch.randn((160, POP, 1, I), device=dev, generator=gen)[:8]
+    y = torch.empty((8, POP, 1, O), device=dev)
+    for s in range(4):
+        neat.neat_forward_lanes(lanes, POP, d, x[s], y[s], stage_bytes=info.max_warp_bytes)
+    cache = neat.LanesCache()
+    neat.neat_forward_lanes_steps(lanes, POP, d, x, y, cache, stage_bytes=info.max_warp_bytes)
+    torch.cuda.synchronize(dev)
+    cache.close()
+    print(json.dumps({"profile": "ant", "warps": info.warps, "stage_bytes": info.max_warp_bytes,
+                      "program_bytes": lane_program_bytes(lanes, info)}), flush=True)
 
 
 def lane_program_bytes(lanes, info) -> int:
