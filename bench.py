@@ -1055,13 +1055,15 @@ def main():
     cache = neat.LanesCache()
     L_plain = neat.neat_default_launch(POP, d, 1)
 
-    # the lane programs' shared-memory stage: the largest warp program of this
-    # population (read once; every later pack of the same genomes gives the same)
+    # the lane programs' shared-memory reservation per block, chosen once
+    # before the timed region by neat_lanes_tune (graphs of 64 steps timed at
+    # each number of blocks per SM); every later pack of the same genomes
+    # gives the same programs
     neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
     neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
     torch.cuda.synchronize(dev)
     info = neat.neat_lanes_query(lanes)
-    stage = info.max_warp_bytes
+    stage = neat.neat_lanes_tune(lanes, POP, d, obs, act, stream=stream)
 
     def episode_batched():
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
@@ -1249,7 +1251,8 @@ def main():
                    "form": "batched: lane programs (neat_lanes_pack once per episode), the 1000 steps as one CUDA "
                            "graph with programmatic dependent launch (neat_forward_lanes_steps)",
                    "launch": {"warps": info.warps, "threads_per_block": 32, "genomes_per_warp": 16,
-                              "stage_bytes": stage}},
+                              "stage_bytes": stage, "largest_program_bytes": info.max_warp_bytes,
+                              "stage_bytes_from": "neat_lanes_tune (untimed, before the warm-up)"}},
         "plain": {"value": value_plain, "unit": UNIT, "episodes": n_plain,
                   "step_p50_ms": float(np.percentile(step_ms, 50)), "step_p99_ms": float(np.percentile(step_ms, 99)),
                   "form": "one neat_forward launch per step from the host (level-walk kernel)"},

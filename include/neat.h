@@ -324,8 +324,10 @@ NEAT_API int neat_lanes_query(const void *lanes_dev, neat_lanes_info *out_host);
 /* One forward from lane programs: inputs f32 [pop][I] -> outputs f32
  * [pop][O] (genome order; NaN for genomes with an error bit).  Each warp
  * program is copied into shared memory when it fits stage_bytes (0: the
- * smaller of warp_stride and 64 KB); a larger one is read from device
- * memory (same results, slower).  pop and d must be those of the pack.
+ * smaller of warp_stride and 48 KB); a larger one is read from device
+ * memory (same results, slower).  stage_bytes is also the shared memory
+ * each block reserves for its program, so it sets how many blocks share an
+ * SM (neat_lanes_tune picks it).  pop and d must be those of the pack.
  * Errors: NEAT_EINVAL, NEAT_ECUDA. */
 NEAT_API int neat_forward_lanes(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
                                 float *outputs_dev, uint32_t stage_bytes, void *stream);
@@ -334,15 +336,30 @@ NEAT_API int neat_forward_lanes(const void *lanes_dev, int32_t pop, neat_dims d,
  * inputs_dev + s * in_step_stride and writing outputs_dev + s *
  * out_step_stride floats; every step after the first launches with
  * programmatic dependent launch (its programs are staged while the previous
- * step drains; its inputs are read after the previous step completes).  The
- * graph is built on first use, kept in *cache (initialise to NULL; free with
- * neat_lanes_cache_destroy) and rebuilt when an argument changes.  Repacking
- * the same lanes buffer between replays is allowed. */
+ * step drains; its inputs are read after the previous step completes; the
+ * next step's input rows are prefetched into L2 one step ahead, a hint that
+ * changes no result).  The graph is built on first use, kept in *cache
+ * (initialise to NULL; free with neat_lanes_cache_destroy) and rebuilt when
+ * an argument changes.  Repacking the same lanes buffer between replays is
+ * allowed. */
 typedef struct neat_lanes_cache neat_lanes_cache;
 NEAT_API int neat_forward_lanes_steps(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
                                       int64_t in_step_stride, float *outputs_dev, int64_t out_step_stride,
                                       int32_t steps, uint32_t stage_bytes, neat_lanes_cache **cache, void *stream);
 NEAT_API void neat_lanes_cache_destroy(neat_lanes_cache *cache);
+
+/* Picks stage_bytes for neat_forward_lanes_steps on this population and
+ * device: one candidate per number of blocks an SM holds (the smallest
+ * reservation for each, from the most the largest program allows down to
+ * the fewest that still hold one step's blocks at once); each is timed as a
+ * graph of min(steps, 64) forwards on `stream` (best of three replays; the
+ * forwards write outputs_dev as neat_forward_lanes_steps does) and the
+ * fastest is written to *stage_bytes.  Arguments as for
+ * neat_forward_lanes_steps; synchronous (reads the pack's header and waits
+ * for the timed graphs).  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+NEAT_API int neat_lanes_tune(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                             int64_t in_step_stride, float *outputs_dev, int64_t out_step_stride, int32_t steps,
+                             uint32_t *stage_bytes, void *stream);
 
 /*
  * Device error word of the forward (single-step, fused and lane-program), plan, CPPN, recurrent and distance kernels: bit 0 is set when a

@@ -39,11 +39,14 @@
 // rule; outputs are bit-identical to neat_forward's.
 //
 // Per step: lane 0 bulk-copies the warp's program (TMA) into shared memory
-// and every lane prefetches its inputs into L2 before the programmatic-
-// dependence wait; after it the inputs are loaded in one round trip, the
-// beats run, and the outputs are written.
+// and the lanes prefetch the genome's inputs into L2 before the programmatic-
+// dependence wait (in a graph of steps also the next step's, one step ahead:
+// an L2 hit after the wait costs about 450 ns, a miss to HBM about 300 ns
+// more); after it the inputs are loaded in one round trip, the beats run,
+// and the outputs are written.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "neat_device.cuh"
 #include "neat_internal.h"
@@ -65,6 +68,7 @@ constexpr uint32_t kLanesMagic = 0x3250414eu;          // "NAP2"
 constexpr uint32_t kWarpSbOff = 16u + 32u * 8u;        // warp header, lane table
 constexpr uint32_t kRowBytes = 32u * 24u;              // one quad per lane: 4 weights, 4 u16 offsets
 constexpr uint32_t kPadRows = 3;                       // padding quads: sum/mean, product, max
+constexpr uint32_t kLaneBar = 16;                      // forward's shared memory: mbarrier, then the value tile
 constexpr uint32_t kLaneError = 1u;                    // genome has an error bit: outputs NaN
 constexpr uint32_t kLaneUnordered = 2u;                // no feedforward schedule (cyclic record): outputs NaN
 constexpr uint32_t kWarpFast = 1u;                     // every genome of the warp is sum + tanh
@@ -443,8 +447,10 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
     if (flags == kLaneUnordered && k == 0) atomicAdd(&hdr->unordered, 1u);
     const unsigned FULL = 0xffffffffu;
     const int nbw = (int)__reduce_max_sync(FULL, (unsigned)nb);
-    const int rows_w = (int)kPadRows + (int)__reduce_max_sync(FULL, (unsigned)my_quads);
     const bool fast_w = __all_sync(FULL, fast);
+    // a warp whose nodes all sum needs only the sum padding quad
+    const uint32_t pad_rows = fast_w ? 1u : kPadRows;
+    const int rows_w = (int)pad_rows + (int)__reduce_max_sync(FULL, (unsigned)my_quads);
     const uint4 *nodes = reinterpret_cast<const uint4 *>(srec + kHeaderBytes);
     const uint2 *edges = reinterpret_cast<const uint2 *>(srec + h1.y);
 
@@ -462,11 +468,11 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
     const uint32_t zero_off = (uint32_t)N * 128u + col4, one_off = (uint32_t)(N + 1) * 128u + col4;
     const uint32_t junk_off = (uint32_t)(N + 2) * 128u + col4;
     uint8_t *rows = wp + off_rows + 24u * (uint32_t)lane;
-    // padding quads: rows 0 (sum, mean), 1 (product), 2 (max)
+    // padding quads: rows 0 (sum, mean), 1 (product), 2 (max); row 0 alone in a fast warp
     {
         const float pw[3] = {-0.0f, 1.0f, __int_as_float(0x7fc00000)};
         const uint32_t ps[3] = {zero_off, one_off, zero_off};
-        for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < (int)pad_rows; ++r) {
             uint2 *q = reinterpret_cast<uint2 *>(rows + (size_t)r * kRowBytes);
             q[0] = make_uint2(__float_as_uint(pw[r]), __float_as_uint(pw[r]));
             q[1] = q[0];
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
     }
     uint32_t *sbt = reinterpret_cast<uint32_t *>(wp + kWarpSbOff);
     uint4 *nrow = reinterpret_cast<uint4 *>(wp + off_node) + lane;
-    uint32_t row = kPadRows;
+    uint32_t row = pad_rows;
     for (int b = 0; b < nbw; ++b) {
         const int p = b < nb ? sched[b * kLaneG + k] : 0xff;
         uint4 ent = make_uint4(0u, 0u, junk_off, 0u);   // unused slot: no edges, identity, sum
@@ -536,8 +542,9 @@ struct LanesArgs {
     const uint8_t *lanes;
     uint64_t warp_base, warp_stride;
     const float *x;          // [pop][I]
+    const float *x_next;     // the next step's inputs [pop][I] (an L2 prefetch hint) or null
     float *y;                // [pop][O]
-    int I, O, N;
+    int pop, I, O, N;
     uint32_t cap;            // shared-memory bytes reserved for a warp's program
 };
 
@@ -637,10 +644,10 @@ __device__ __forceinline__ Quad lds_quad(uint32_t a)
                  : "r"(a));
     return q;
 }
-// Value at byte offset `off` of the tile (the tile sits 128 bytes into the
-// block's dynamic shared memory).
-__device__ __forceinline__ float tile_ld(uint32_t off) { return *reinterpret_cast<const float *>(lane_sm + 128 + off); }
-__device__ __forceinline__ void tile_st(uint32_t off, float v) { *reinterpret_cast<float *>(lane_sm + 128 + off) = v; }
+// Value at byte offset `off` of the tile (the tile sits kLaneBar bytes into
+// the block's dynamic shared memory).
+__device__ __forceinline__ float tile_ld(uint32_t off) { return *reinterpret_cast<const float *>(lane_sm + kLaneBar + off); }
+__device__ __forceinline__ void tile_st(uint32_t off, float v) { *reinterpret_cast<float *>(lane_sm + kLaneBar + off) = v; }
 
 __device__ __forceinline__ void fma_quad(const Quad &q, float &p0, float &p1, float &p2, float &p3)
 {
@@ -653,12 +660,14 @@ __device__ __forceinline__ void fma_quad(const Quad &q, float &p0, float &p1, fl
 }
 
 // State carried from one beat to the next in the fast walk: the beat's node
-// entry, its quad count and first row address, and its first two rows
-// (loaded during the previous beat).
+// entry, its quad count and first row address, and its first kHeadRows rows
+// (loaded during the previous beat, so that after the warp barrier only the
+// value loads stand between a beat and its multiply-adds).
+constexpr int kHeadRows = 4;
 struct BeatState {
     uint4 ne;
     uint32_t mt, base;
-    Quad q0, q1;
+    Quad q[kHeadRows];
 };
 
 __device__ __forceinline__ void load_beat_head(BeatState &st, uint4 ne, uint32_t ra)
@@ -666,16 +675,16 @@ __device__ __forceinline__ void load_beat_head(BeatState &st, uint4 ne, uint32_t
     st.ne = ne;
     st.mt = ((ne.w & 0xffffu) + 3u) >> 2;
     st.base = ra + (ne.z >> 16) * kRowBytes;
-    st.q0 = lds_quad(0u < st.mt ? st.base : ra);
-    st.q1 = lds_quad(1u < st.mt ? st.base + kRowBytes : ra);
+#pragma unroll
+    for (int t = 0; t < kHeadRows; ++t) st.q[t] = lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
 }
 
 // `len` beats from beat b on, every one with T trips (T even, known at
-// compile time; T = 0: nodes without edges).  Per beat: rows 2..T-1 loaded
-// (rows 0 and 1 are in the state), then the values and the fused
+// compile time; T = 0: nodes without edges).  Per beat: rows kHeadRows..T-1
+// loaded (the first rows are in the state), then the values and the fused
 // multiply-adds in trip order per partial; the next beat's head (entry and
-// first two rows) is loaded before the node rule, the store of the value
-// into every column of the genome and the warp barrier.  A lane past its own
+// first rows) is loaded before the node rule, the store of the value into
+// every column of the genome and the warp barrier.  A lane past its own
 // quads reads the padding quad at `ra`.
 template <int T>
 __device__ __forceinline__ void run_beats(BeatState &st, int b, int len, int nb, uint32_t na, uint32_t ra, int lane)
@@ -685,10 +694,10 @@ __device__ __forceinline__ void run_beats(BeatState &st, int b, int len, int nb,
         float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
         if (T > 0) {
             Quad q[T > 0 ? T : 1];
-            q[0] = st.q0;
-            if (T > 1) q[1] = st.q1;
 #pragma unroll
-            for (int t = 2; t < T; ++t) q[t] = lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
+            for (int t = 0; t < T; ++t)
+                q[t] = t < kHeadRows ? st.q[t < kHeadRows ? t : 0]
+                                     : lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
 #pragma unroll
             for (int t = 0; t < T; ++t) fma_quad(q[t], p0, p1, p2, p3);
         }
@@ -702,18 +711,17 @@ __device__ __forceinline__ void run_beats(BeatState &st, int b, int len, int nb,
     }
 }
 
-// The same for any even T (trip pairs in a loop).
+// The same for any even T above 8 (trip pairs in a loop after the head rows).
 __device__ __forceinline__ void run_beats_any(BeatState &st, int T, int b, int len, int nb, uint32_t na, uint32_t ra,
                                            int lane)
 {
     for (int i = 0; i < len; ++i, ++b) {
         const uint4 nn = b + 1 < nb ? lds_u4(na + 512u * (uint32_t)(b + 1)) : st.ne;
         float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
-        if (T > 0) {
-            fma_quad(st.q0, p0, p1, p2, p3);
-            fma_quad(st.q1, p0, p1, p2, p3);
-        }
-        for (int t = 2; t < T; t += 2) {
+#pragma unroll
+        for (int t = 0; t < kHeadRows; ++t)
+            if (t < T) fma_quad(st.q[t], p0, p1, p2, p3);
+        for (int t = kHeadRows; t < T; t += 2) {
             const Quad qa = lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
             const Quad qb = lds_quad((uint32_t)t + 1u < st.mt ? st.base + (uint32_t)(t + 1) * kRowBytes : ra);
             fma_quad(qa, p0, p1, p2, p3);
@@ -758,18 +766,74 @@ __device__ __forceinline__ void walk_fast_staged(uint32_t P, int nb, int lane)
     }
 }
 
-constexpr int kLaneInputRegs = 32;
+// Chunks of 16 bytes a lane holds in registers while it loads inputs.
+constexpr int kLaneInputChunks = 4;
 
-// Shared memory of the forward: [0, 128) mbarrier | value tile (N + 3) x 32
-// floats | program (cap bytes).
+// The genome's inputs into both of its columns of the value tile.  The row
+// of I floats is read as the 16-byte-aligned chunks that cover it, the
+// genome's two lanes taking alternate chunks (adjacent chunks of one row in
+// one instruction, so that a load touches about one L1 line per genome
+// instead of one per genome and float); each lane stores the words of its
+// chunks into its own column and its partner's.  A chunk that reaches
+// outside the input array [x, x_end) is read word by word, the row's words
+// only.  Lanes without a genome store zeros.
+__device__ __forceinline__ void load_inputs(const float *__restrict__ x, const float *x_end, int g, int I, int lane,
+                                            float *V)
+{
+    if (I <= 0) return;
+    const int half = lane / kLaneJ;
+    const int mate = (lane + kLaneJ) & 31;
+    const uintptr_t ra = reinterpret_cast<uintptr_t>(x + (size_t)(g >= 0 ? g : 0) * I);
+    const float4 *w = reinterpret_cast<const float4 *>(ra & ~(uintptr_t)15);
+    const int mis = g >= 0 ? (int)((ra & 15u) >> 2) : 0;
+    const int nch = (mis + I + 3) >> 2;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(x), hi = reinterpret_cast<uintptr_t>(x_end);
+    for (int c0 = 0; c0 < nch; c0 += 2 * kLaneInputChunks) {
+        float4 r[kLaneInputChunks];
+#pragma unroll
+        for (int k = 0; k < kLaneInputChunks; ++k) {
+            const int c = c0 + 2 * k + half;
+            r[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (g >= 0 && c < nch) {
+                const float4 *p = w + c;
+                const uintptr_t pa = reinterpret_cast<uintptr_t>(p);
+                if (pa >= lo && pa + 16u <= hi) {
+                    r[k] = __ldg(p);
+                } else {
+                    const float *pf = reinterpret_cast<const float *>(p);
+                    const int j = 4 * c - mis;
+                    if (j >= 0 && j < I) r[k].x = __ldg(pf);
+                    if (j + 1 >= 0 && j + 1 < I) r[k].y = __ldg(pf + 1);
+                    if (j + 2 >= 0 && j + 2 < I) r[k].z = __ldg(pf + 2);
+                    if (j + 3 >= 0 && j + 3 < I) r[k].w = __ldg(pf + 3);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kLaneInputChunks; ++k) {
+            const int j = 4 * (c0 + 2 * k + half) - mis;
+            const float e[4] = {r[k].x, r[k].y, r[k].z, r[k].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j + q >= 0 && j + q < I) {
+                    V[(j + q) * 32 + lane] = e[q];
+                    V[(j + q) * 32 + mate] = e[q];
+                }
+        }
+    }
+}
+
+// Shared memory of the forward: [0, 16) mbarrier | value tile (N + 3) x 32
+// floats | program (cap bytes).  (At Ant size a block takes 36.3 KB with the
+// 1 KB the runtime reserves per block: six blocks per SM.)
 __host__ __device__ inline uint32_t lanes_tile_bytes(int N) { return (uint32_t)(N + 3) * 128u; }
 
 template <bool PDL>
 __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
 {
     unsigned char *sm = lane_sm;
-    float *V = reinterpret_cast<float *>(sm + 128);
-    unsigned char *sprog = sm + 128 + lanes_tile_bytes(a.N);
+    float *V = reinterpret_cast<float *>(sm + kLaneBar);
+    unsigned char *sprog = sm + kLaneBar + lanes_tile_bytes(a.N);
     const int lane = threadIdx.x;
     const unsigned char *gw = a.lanes + a.warp_base + (size_t)blockIdx.x * a.warp_stride;
     const uint4 wh = __ldg(reinterpret_cast<const uint4 *>(gw));
@@ -783,28 +847,21 @@ __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
         bulk_g2s(smem_addr(sprog), gw, bytes, bar);
     }
     const int g = li.x;
-    const float *xg = a.x + (size_t)(g >= 0 ? g : 0) * a.I;
+    // the inputs into L2 while the previous kernel finishes, the lower lane
+    // of the genome this step's row, the upper one the next step's (a hint:
+    // L2 is the point of coherence, no L1 line is filled)
+    const float *xp = lane < kLaneJ ? (PDL ? a.x : nullptr) : a.x_next;
+    if (g >= 0 && a.I > 0 && xp) {
+        const char *p0 = reinterpret_cast<const char *>(xp + (size_t)g * a.I);
+        const char *p1 = p0 + 4u * (uint32_t)a.I - 1;
+        for (const char *p = p0; p <= p1; p += 128) prefetch_l2(p);
+        prefetch_l2(p1);
+    }
     if constexpr (PDL) {
-        // the inputs into L2 while the previous kernel finishes (a hint:
-        // L2 is the point of coherence, no L1 line is filled)
-        if (g >= 0 && a.I > 0 && lane < kLaneJ) {
-            const char *p0 = reinterpret_cast<const char *>(xg);
-            const char *p1 = reinterpret_cast<const char *>(xg + a.I) - 1;
-            for (const char *p = p0; p <= p1; p += 128) prefetch_l2(p);
-            prefetch_l2(p1);
-        }
         pdl_wait();
         pdl_trigger();
     }
-    // inputs into this lane's column: up to 32 loads in flight before the first store
-    for (int j0 = 0; j0 < a.I; j0 += kLaneInputRegs) {
-        float xr[kLaneInputRegs];
-#pragma unroll
-        for (int k = 0; k < kLaneInputRegs; ++k) xr[k] = (g >= 0 && j0 + k < a.I) ? __ldg(xg + j0 + k) : 0.0f;
-#pragma unroll
-        for (int k = 0; k < kLaneInputRegs; ++k)
-            if (j0 + k < a.I) V[(j0 + k) * 32 + lane] = xr[k];
-    }
+    load_inputs(a.x, a.x + (size_t)a.pop * a.I, g, a.I, lane, V);
     V[a.N * 32 + lane] = 0.0f;
     V[(a.N + 1) * 32 + lane] = 1.0f;
     bool ok = true;
@@ -830,8 +887,17 @@ __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
     if (g >= 0) {
         float *yg = a.y + (size_t)g * a.O;
         const bool nan_out = !ok || (li.y & (int)(kLaneError | kLaneUnordered));
-        for (int j = lane / kLaneJ; j < a.O; j += kLaneG)
-            yg[j] = nan_out ? __int_as_float(0x7fc00000) : V[(a.I + j) * 32 + lane];
+        const float qnan = __int_as_float(0x7fc00000);
+        if ((a.O & 3) == 0 && (reinterpret_cast<uintptr_t>(a.y) & 15u) == 0) {
+            // 16-byte stores, the genome's two lanes alternating
+            for (int j = 4 * (lane / kLaneJ); j < a.O; j += 4 * kLaneG) {
+                const float *v = V + (a.I + j) * 32 + lane;
+                *reinterpret_cast<float4 *>(yg + j) = nan_out ? make_float4(qnan, qnan, qnan, qnan)
+                                                              : make_float4(v[0], v[32], v[64], v[96]);
+            }
+        } else {
+            for (int j = lane / kLaneJ; j < a.O; j += kLaneG) yg[j] = nan_out ? qnan : V[(a.I + j) * 32 + lane];
+        }
     }
 }
 
@@ -843,7 +909,7 @@ uint32_t default_cap(const LanesGeom &g)
 int launch_lanes(const LanesArgs &a, int warps, bool pdl, cudaStream_t s)
 {
     if (warps == 0) return NEAT_OK;
-    const size_t smem = 128u + lanes_tile_bytes(a.N) + a.cap;
+    const size_t smem = kLaneBar + lanes_tile_bytes(a.N) + a.cap;
     auto f = pdl ? lanes_kernel<true> : lanes_kernel<false>;
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(f), smem, "neat_forward_lanes: shared memory per block");
     if (rc) return rc;
@@ -878,12 +944,14 @@ int make_lanes_args(const void *lanes, int32_t pop, const neat_dims &d, const fl
     a.warp_base = g.warp_base;
     a.warp_stride = g.warp_stride;
     a.x = x;
+    a.x_next = nullptr;
     a.y = y;
+    a.pop = pop;
     a.I = d.num_inputs;
     a.O = d.num_outputs;
     a.N = d.max_nodes;
     a.cap = cap ? align16(std::min<uint32_t>(cap, (uint32_t)g.warp_stride)) : default_cap(g);
-    if (128u + lanes_tile_bytes(a.N) + a.cap > kMaxSmemPerBlock) return invalid("neat_forward_lanes: stage_bytes too large");
+    if (kLaneBar + lanes_tile_bytes(a.N) + a.cap > kMaxSmemPerBlock) return invalid("neat_forward_lanes: stage_bytes too large");
     *out = a;
     *warps = g.warps;
     return NEAT_OK;
@@ -1034,6 +1102,7 @@ extern "C" int neat_forward_lanes_steps(const void *lanes_dev, int32_t pop, neat
         for (int st = 0; st < steps && rc == NEAT_OK; ++st) {
             LanesArgs as = a;
             as.x = inputs_dev ? inputs_dev + (size_t)st * in_step_stride : nullptr;
+            as.x_next = inputs_dev && st + 1 < steps ? inputs_dev + (size_t)(st + 1) * in_step_stride : nullptr;
             as.y = outputs_dev + (size_t)st * out_step_stride;
             rc = launch_lanes(as, warps, st > 0, c.cap_stream);   // the first step fully waits for prior work
         }
@@ -1071,6 +1140,81 @@ extern "C" void neat_lanes_cache_destroy(neat_lanes_cache *c)
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
+}
+
+extern "C" int neat_lanes_tune(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                               int64_t in_step_stride, float *outputs_dev, int64_t out_step_stride, int32_t steps,
+                               uint32_t *stage_bytes, void *stream)
+{
+    TraceRange trace_range("neat_lanes_tune");
+    clear_error();
+    if (!stage_bytes) return invalid("neat_lanes_tune: null stage_bytes");
+    if (steps < 1) return invalid("neat_lanes_tune: steps < 1");
+    LanesArgs a;
+    int warps = 0;
+    int rc = make_lanes_args(lanes_dev, pop, d, inputs_dev, outputs_dev, 0, &a, &warps);
+    if (rc) return rc;
+    cudaStream_t s = as_stream(stream);
+    LanesHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, lanes_dev, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_lanes_tune: read header");
+    if (h.magic != kLanesMagic || h.pop != pop) return invalid("neat_lanes_tune: lanes buffer not packed for this pop");
+    const uint32_t first = align16(std::max<uint32_t>(h.max_warp_bytes, 16u));
+    *stage_bytes = first;
+    if (warps == 0) return NEAT_OK;
+    // candidates: the smallest reservation for each number of resident
+    // blocks per SM, from the most the largest program allows down to the
+    // fewest that still hold one step's blocks in one wave
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t tile = lanes_tile_bytes(d.max_nodes);
+    const uint32_t last = (uint32_t)std::min<uint64_t>(h.warp_stride, kMaxSmemPerBlock - kLaneBar - tile);
+    rc = allow_dynamic_smem(reinterpret_cast<const void *>(lanes_kernel<true>), kLaneBar + tile + last,
+                            "neat_lanes_tune: shared memory per block");
+    if (rc) return rc;
+    std::vector<uint32_t> caps;
+    int prev = -1;
+    for (uint32_t cap = first; cap <= last; cap += 128u) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanes_kernel<true>, 32, kLaneBar + tile + cap);
+        if (e != cudaSuccess) return cuda_fail(e, "neat_lanes_tune: occupancy");
+        if ((int64_t)occ * sms < warps) break;
+        if (occ != prev) caps.push_back(cap);
+        prev = occ;
+    }
+    if (caps.size() <= 1) return NEAT_OK;
+    // time a graph of up to 64 steps at each candidate (best of three)
+    const int n = std::min(steps, 64);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 0.0f;
+    for (uint32_t cap : caps) {
+        neat_lanes_cache *c = nullptr;
+        float ms_min = 0.0f;
+        for (int r = 0; r < 4 && rc == NEAT_OK; ++r) {
+            cudaEventRecord(e0, s);
+            rc = neat_forward_lanes_steps(lanes_dev, pop, d, inputs_dev, in_step_stride, outputs_dev, out_step_stride,
+                                          n, cap, &c, stream);
+            cudaEventRecord(e1, s);
+            e = cudaEventSynchronize(e1);
+            if (rc == NEAT_OK && e != cudaSuccess) rc = cuda_fail(e, "neat_lanes_tune: timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && (r == 1 || ms < ms_min)) ms_min = ms;     // the first run captures the graph
+        }
+        neat_lanes_cache_destroy(c);
+        if (rc) break;
+        if (cap == caps.front() || ms_min < best_ms) {
+            best_ms = ms_min;
+            *stage_bytes = cap;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 namespace neat {

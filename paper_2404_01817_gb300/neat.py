@@ -162,6 +162,7 @@ _sig = {
     "neat_forward_lanes_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _P, _i64, _i32, ctypes.c_uint32,
                                                 ctypes.POINTER(_P), _P]),
     "neat_lanes_cache_destroy": (None, [_P]),
+    "neat_lanes_tune": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _P, _i64, _i32, ctypes.POINTER(ctypes.c_uint32), _P]),
     "neat_forward_fused": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _i32, _P, _i64, _i32, ctypes.POINTER(Launch), _P]),
     "neat_plan_create": (ctypes.c_int, [ctypes.POINTER(PopDesc), _i32, ctypes.POINTER(PlanOptions), _P,
                                         ctypes.POINTER(_P)]),
@@ -561,6 +562,18 @@ def neat_forward_lanes_steps(lanes, pop: int, d: Dims, inputs, outputs, cache: L
                                          pop * d.num_outputs, steps, stage_bytes, ctypes.byref(cache.handle),
                                          _stream(stream)), "neat_forward_lanes_steps")
     return outputs
+
+
+def neat_lanes_tune(lanes, pop: int, d: Dims, inputs, outputs, stream=None) -> int:
+    """stage_bytes for neat_forward_lanes_steps, timed on these arrays
+    (inputs [S][P][...][I], outputs [S][P][...][O]; writes outputs)."""
+    steps = inputs.shape[0]
+    assert inputs.shape[1] == pop and outputs.shape[0] == steps and outputs.shape[1] == pop
+    assert inputs.is_contiguous() and outputs.is_contiguous()
+    sb = ctypes.c_uint32(0)
+    _check(_lib.neat_lanes_tune(_ptr(lanes), pop, d, _ptr(inputs), pop * d.num_inputs, _ptr(outputs),
+                                pop * d.num_outputs, steps, ctypes.byref(sb), _stream(stream)), "neat_lanes_tune")
+    return int(sb.value)
 
 
 class Plan:

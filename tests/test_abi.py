@@ -132,3 +132,10 @@ def test_lane_program_sizes_and_argument_errors(lib_path):
     assert lib.neat_forward_lanes(128, 4, d, None, 16, 0, None) == neat.NEAT_EINVAL      # I > 0 without inputs
     assert lib.neat_forward_lanes(128, 4, neat.dims(8, 4, 129, 200), 16, 16, 0, None) == neat.NEAT_EINVAL
     assert lib.neat_forward_lanes_steps(128, 4, d, 16, 27, 16, 8, -1, 0, None, None) == neat.NEAT_EINVAL
+    # tune: the output pointer, the step count and the pointers are checked before any device call
+    import ctypes
+    sb = ctypes.c_uint32(0)
+    assert lib.neat_lanes_tune(128, 4, d, 16, 108, 16, 32, 4, None, None) == neat.NEAT_EINVAL
+    assert lib.neat_lanes_tune(128, 4, d, 16, 108, 16, 32, 0, ctypes.byref(sb), None) == neat.NEAT_EINVAL
+    assert lib.neat_lanes_tune(None, 4, d, 16, 108, 16, 32, 4, ctypes.byref(sb), None) == neat.NEAT_EINVAL
+    assert lib.neat_lanes_tune(64, 4, d, 16, 108, 16, 32, 4, ctypes.byref(sb), None) == neat.NEAT_EINVAL  # alignment

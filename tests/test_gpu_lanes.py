@@ -88,6 +88,33 @@ def test_lanes_program_from_device_memory(neat):
     np.testing.assert_array_equal(y_staged, y_global)
 
 
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_lanes_inputs_not_16_byte_aligned(neat, shift):
+    """Inputs and outputs that start 4, 8 or 12 bytes past a 16-byte
+    boundary: the input chunks that cover the first and last rows reach
+    outside the array and are read word by word, the outputs are stored word
+    by word; the outputs keep their bits."""
+    import torch
+    pop = W.ant_population(6, 203)
+    d, rec, lanes = _prepare(neat, pop)
+    x = W.normal_inputs(9, (203, 27))
+    buf = torch.zeros(203 * 27 + 8, device="cuda")
+    view = buf[shift:shift + 203 * 27].view(203, 27)
+    view.copy_(_dev(x))
+    assert view.data_ptr() % 16 == 4 * shift
+    y = neat.neat_forward_lanes(lanes, 203, d, view).cpu().numpy()
+    ybuf = torch.full((203 * 8 + 4,), float("inf"), device="cuda")
+    yview = ybuf[shift:shift + 203 * 8].view(203, 8)
+    neat.neat_forward_lanes(lanes, 203, d, view, outputs=yview)
+    np.testing.assert_array_equal(yview.cpu().numpy(), y)
+    assert np.isinf(ybuf[:shift].cpu().numpy()).all() and np.isinf(ybuf[shift + 203 * 8:].cpu().numpy()).all()
+    y_plain = neat.neat_forward(rec, 203, d, _dev(x[:, None, :])).cpu().numpy().reshape(203, 8)
+    np.testing.assert_array_equal(y, y_plain)
+    for i in (0, 202):                         # the array's first and last rows
+        ref = oracle.forward(pop.nodes[i:i + 1], pop.conns[i:i + 1], 27, 8, x[i:i + 1, None, :])
+        assert_outputs_close(y[i:i + 1], ref[:, 0], what=f"row {i}")
+
+
 def _malformed(seed, n):
     """Small genomes, every fourth with a planted error (cycle, duplicate key,
     missing output), the rest valid with warnings (dangling, into-input)."""
@@ -193,6 +220,27 @@ def test_lanes_steps_graph_matches_per_step(neat):
     torch.cuda.synchronize()
     for s in range(S):
         np.testing.assert_array_equal(y[s].cpu().numpy(), neat.neat_forward(rec, 1000, d, x[s]).cpu().numpy())
+    cache.close()
+
+
+def test_lanes_tune_picks_a_staging_capacity(neat):
+    """neat_lanes_tune returns a stage_bytes that stages every program; the
+    graph at that capacity gives the same bits."""
+    import torch
+    pop = W.ant_population(7, 3000)
+    d, rec, lanes = _prepare(neat, pop)
+    info = neat.neat_lanes_query(lanes)
+    S = 16
+    x = _dev(W.normal_inputs(10, (S, 3000, 1, 27)))
+    y = torch.empty((S, 3000, 1, 8), device="cuda")
+    sb = neat.neat_lanes_tune(lanes, 3000, d, x, y)
+    assert sb % 16 == 0 and info.max_warp_bytes <= sb <= info.warp_stride
+    y2 = torch.empty_like(y)
+    cache = neat.LanesCache()
+    neat.neat_forward_lanes_steps(lanes, 3000, d, x, y2, cache, stage_bytes=sb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y2.cpu().numpy(), y.cpu().numpy())
+    np.testing.assert_array_equal(y2[S - 1].cpu().numpy(), neat.neat_forward(rec, 3000, d, x[S - 1]).cpu().numpy())
     cache.close()
 
 
