@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--env-steps", type=int, default=ENV_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other four workloads in the default run")
+    ap.add_argument("--stage-bytes", type=int, default=0,
+                    help="Ant: the lane programs' staging reservation (0: chosen by neat_lanes_tune before the "
+                         "warm-up); a fixed value keeps the launch sequence fixed for ncu launch lists")
     ap.add_argument("--profile", action="store_true",
                     help="short case for ncu (ant: transform, lane compile, 4 forwards, an 8-step graph; "
                          "batched: one plan step); no timing")
@@ -1063,7 +1066,7 @@ def main():
     neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
     torch.cuda.synchronize(dev)
     info = neat.neat_lanes_query(lanes)
-    stage = neat.neat_lanes_tune(lanes, POP, d, obs, act, stream=stream)
+    stage = args.stage_bytes or neat.neat_lanes_tune(lanes, POP, d, obs, act, stream=stream)
 
     def episode_batched():
         neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
@@ -1133,10 +1136,13 @@ def main():
 
     # ---- end to end through the C ABI: host genome tensors and observations
     # in, actions out, every episode.  The episode is cut into chunks (a short
-    # first one, so compute starts early): chunk c's observations upload on a
-    # copy stream as soon as the previous episode's chunk c has been consumed
-    # (its forward and its action download), so uploads run ahead of the
-    # compute, and chunk c's actions download behind it.
+    # first one, so compute starts early).  Uploads run on one copy stream,
+    # downloads on another, so that the two directions overlap each other and
+    # the compute: chunk c's observations upload as soon as the previous
+    # episode's chunk-c forward has read its buffer (uploads keep running
+    # ahead, across episodes), chunk c's forward waits for its upload and for
+    # the previous episode's download of its action buffer, and chunk c's
+    # actions download behind its forward.
     nodes_h = torch.from_numpy(pop.nodes).pin_memory()
     conns_h = torch.from_numpy(pop.conns).pin_memory()
     obs_h = obs.cpu().pin_memory()
@@ -1145,38 +1151,52 @@ def main():
     bounds = sorted(set(bounds))
     CH = len(bounds) - 1
     chunk_caches = [neat.LanesCache() for _ in range(CH)]
-    copy_stream = torch.cuda.Stream(dev)
-    prev_used = [None] * CH      # events: the previous episode is done with chunk c's buffers
+    up_stream = torch.cuda.Stream(dev)
+    down_stream = torch.cuda.Stream(dev)
+    prev_fwd = [None] * CH       # the previous episode's chunk-c forward (done reading obs chunk c)
+    prev_dl = [None] * CH        # the previous episode's chunk-c download (done reading act chunk c)
+    prev_tr = [None]             # the previous episode's transform (done reading the genome tensors)
 
     def episode_e2e():
+        ev_gen, ev_tr = torch.cuda.Event(), torch.cuda.Event()
         ev_in = [torch.cuda.Event() for _ in range(CH)]
         ev_done = [torch.cuda.Event() for _ in range(CH)]
         ev_dl = [torch.cuda.Event() for _ in range(CH)]
-        nodes.copy_(nodes_h, non_blocking=True)
-        conns.copy_(conns_h, non_blocking=True)
-        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
-        neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
-        with torch.cuda.stream(copy_stream):
+        with torch.cuda.stream(up_stream):
+            # the genomes first, then the observations chunk by chunk
+            if prev_tr[0] is not None:
+                up_stream.wait_event(prev_tr[0])
+            nodes.copy_(nodes_h, non_blocking=True)
+            conns.copy_(conns_h, non_blocking=True)
+            ev_gen.record(up_stream)
             for c in range(CH):
-                if prev_used[c] is not None:
-                    copy_stream.wait_event(prev_used[c])
+                if prev_fwd[c] is not None:
+                    up_stream.wait_event(prev_fwd[c])
                 lo, hi = bounds[c], bounds[c + 1]
                 obs[lo:hi].copy_(obs_h[lo:hi], non_blocking=True)
-                ev_in[c].record(copy_stream)
+                ev_in[c].record(up_stream)
+        stream.wait_event(ev_gen)
+        neat.neat_transform(nodes, conns, d, rec, status, stream=stream)
+        ev_tr.record(stream)
+        prev_tr[0] = ev_tr
+        neat.neat_lanes_pack(rec, POP, d, lanes=lanes, stream=stream)
         for c in range(CH):
             lo, hi = bounds[c], bounds[c + 1]
             stream.wait_event(ev_in[c])
+            if prev_dl[c] is not None:
+                stream.wait_event(prev_dl[c])
             neat.neat_forward_lanes_steps(lanes, POP, d, obs[lo:hi], act[lo:hi], chunk_caches[c], stage_bytes=stage,
                                           stream=stream)
             ev_done[c].record(stream)
-        with torch.cuda.stream(copy_stream):
+        with torch.cuda.stream(down_stream):
             for c in range(CH):
                 lo, hi = bounds[c], bounds[c + 1]
-                copy_stream.wait_event(ev_done[c])
+                down_stream.wait_event(ev_done[c])
                 act_h[lo:hi].copy_(act[lo:hi], non_blocking=True)
-                ev_dl[c].record(copy_stream)
+                ev_dl[c].record(down_stream)
         for c in range(CH):
-            prev_used[c] = ev_dl[c]          # after the download, which follows the forward
+            prev_fwd[c] = ev_done[c]
+            prev_dl[c] = ev_dl[c]
         return ev_dl[CH - 1]
 
     last = episode_e2e()
@@ -1252,7 +1272,8 @@ def main():
                            "graph with programmatic dependent launch (neat_forward_lanes_steps)",
                    "launch": {"warps": info.warps, "threads_per_block": 32, "genomes_per_warp": 16,
                               "stage_bytes": stage, "largest_program_bytes": info.max_warp_bytes,
-                              "stage_bytes_from": "neat_lanes_tune (untimed, before the warm-up)"}},
+                              "stage_bytes_from": "--stage-bytes" if args.stage_bytes else
+                              "neat_lanes_tune (untimed, before the warm-up)"}},
         "plain": {"value": value_plain, "unit": UNIT, "episodes": n_plain,
                   "step_p50_ms": float(np.percentile(step_ms, 50)), "step_p99_ms": float(np.percentile(step_ms, 99)),
                   "form": "one neat_forward launch per step from the host (level-walk kernel)"},
@@ -1262,8 +1283,9 @@ def main():
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
                 "form": f"pinned host genomes and observations in, actions out, every episode (transform, lane "
                         f"compile, forwards); {CH} chunks (the first {bounds[1]} steps, then up to 100): uploads run "
-                        "ahead of the graphs on a copy stream (a chunk's waits for the previous episode to be done "
-                        "with it), downloads behind"},
+                        "ahead of the graphs on their own copy stream, across episodes (a chunk's waits for the "
+                        "previous episode's forward of it), downloads behind on another; copy-bound (about 210 GB/s "
+                        "host to device, 190 back, measured alone)"},
         "fused_multistep": {"value": world * POP * S * n_fused / t_fused, "unit": UNIT, "episodes": n_fused,
                             "us_per_step": t_fused / n_fused / S * 1e6,
                             "form": "one launch per episode (neat_forward_fused, level-walk kernel), records read "
@@ -1312,7 +1334,11 @@ def profile_ant(args, dev):
     """A short Ant case for ncu: transform, lane-program compile, four single
     lane forwards, then an 8-step lane graph (no timing).  Launch order:
     transform, the three compile kernels, lanes_kernel x 4, then the graph's
-    eight lanes_kernel launches."""
+    eight lanes_kernel launches.  The single forwards read other
+    observations than the graph's, and the observations' dirty lines are
+    written back (a read of a buffer larger than L2) before any lane forward,
+    so that each graph launch reads its inputs from HBM and its DRAM
+    counters hold its own traffic only."""
     import torch
     from paper_2404_01817_gb300 import neat
     from paper_2404_01817_gb300 import workloads as W
@@ -1324,15 +1350,14 @@ def profile_ant(args, dev):
     info = neat.neat_lanes_query(lanes)
     gen = torch.Generator(device=dev)
     gen.manual_seed(5)
-    # 160 steps of observations (173 MB, more than L2) drawn in order: the
-    # first 8, used below, have left L2 again, so the forwards read their
-    # inputs from HBM as in the timed episode
-    x = torch.randn((160, POP, 1, I), device=dev, generator=gen)[:8]
-    y = torch.empty((8, POP, 1, O), device=dev)
+    flush = torch.ones(96 << 20, device=dev)                  # 384 MB, allocated before the observations
+    x = torch.randn((12, POP, 1, I), device=dev, generator=gen)
+    y = torch.empty((12, POP, 1, O), device=dev)
+    float(flush.sum())                                         # evicts (writes back) the observations' lines
     for s in range(4):
-        neat.neat_forward_lanes(lanes, POP, d, x[s], y[s], stage_bytes=info.max_warp_bytes)
+        neat.neat_forward_lanes(lanes, POP, d, x[8 + s], y[8 + s], stage_bytes=info.max_warp_bytes)
     cache = neat.LanesCache()
-    neat.neat_forward_lanes_steps(lanes, POP, d, x, y, cache, stage_bytes=info.max_warp_bytes)
+    neat.neat_forward_lanes_steps(lanes, POP, d, x[:8], y[:8], cache, stage_bytes=info.max_warp_bytes)
     torch.cuda.synchronize(dev)
     cache.close()
     print(json.dumps({"profile": "ant", "warps": info.warps, "stage_bytes": info.max_warp_bytes,

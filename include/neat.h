@@ -336,9 +336,8 @@ NEAT_API int neat_forward_lanes(const void *lanes_dev, int32_t pop, neat_dims d,
  * inputs_dev + s * in_step_stride and writing outputs_dev + s *
  * out_step_stride floats; every step after the first launches with
  * programmatic dependent launch (its programs are staged while the previous
- * step drains; its inputs are read after the previous step completes; the
- * next step's input rows are prefetched into L2 one step ahead, a hint that
- * changes no result).  The graph is built on first use, kept in *cache
+ * step drains; its inputs are read after the previous step completes).  The
+ * graph is built on first use, kept in *cache
  * (initialise to NULL; free with neat_lanes_cache_destroy) and rebuilt when
  * an argument changes.  Repacking the same lanes buffer between replays is
  * allowed. */

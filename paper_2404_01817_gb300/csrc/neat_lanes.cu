@@ -40,10 +40,9 @@
 //
 // Per step: lane 0 bulk-copies the warp's program (TMA) into shared memory
 // and the lanes prefetch the genome's inputs into L2 before the programmatic-
-// dependence wait (in a graph of steps also the next step's, one step ahead:
-// an L2 hit after the wait costs about 450 ns, a miss to HBM about 300 ns
-// more); after it the inputs are loaded in one round trip, the beats run,
-// and the outputs are written.
+// dependence wait (the loads after it then take about 0.7 us at Ant size
+// instead of 1.0); after it the inputs are loaded in one round trip, the
+// beats run, and the outputs are written.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -542,7 +541,6 @@ struct LanesArgs {
     const uint8_t *lanes;
     uint64_t warp_base, warp_stride;
     const float *x;          // [pop][I]
-    const float *x_next;     // the next step's inputs [pop][I] (an L2 prefetch hint) or null
     float *y;                // [pop][O]
     int pop, I, O, N;
     uint32_t cap;            // shared-memory bytes reserved for a warp's program
@@ -847,17 +845,15 @@ __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
         bulk_g2s(smem_addr(sprog), gw, bytes, bar);
     }
     const int g = li.x;
-    // the inputs into L2 while the previous kernel finishes, the lower lane
-    // of the genome this step's row, the upper one the next step's (a hint:
-    // L2 is the point of coherence, no L1 line is filled)
-    const float *xp = lane < kLaneJ ? (PDL ? a.x : nullptr) : a.x_next;
-    if (g >= 0 && a.I > 0 && xp) {
-        const char *p0 = reinterpret_cast<const char *>(xp + (size_t)g * a.I);
-        const char *p1 = p0 + 4u * (uint32_t)a.I - 1;
-        for (const char *p = p0; p <= p1; p += 128) prefetch_l2(p);
-        prefetch_l2(p1);
-    }
     if constexpr (PDL) {
+        // the genome's inputs into L2 while the previous kernel finishes (a
+        // hint: L2 is the point of coherence, no L1 line is filled)
+        if (g >= 0 && a.I > 0 && lane < kLaneJ) {
+            const char *p0 = reinterpret_cast<const char *>(a.x + (size_t)g * a.I);
+            const char *p1 = p0 + 4u * (uint32_t)a.I - 1;
+            for (const char *p = p0; p <= p1; p += 128) prefetch_l2(p);
+            prefetch_l2(p1);
+        }
         pdl_wait();
         pdl_trigger();
     }
@@ -944,7 +940,6 @@ int make_lanes_args(const void *lanes, int32_t pop, const neat_dims &d, const fl
     a.warp_base = g.warp_base;
     a.warp_stride = g.warp_stride;
     a.x = x;
-    a.x_next = nullptr;
     a.y = y;
     a.pop = pop;
     a.I = d.num_inputs;
@@ -1102,7 +1097,6 @@ extern "C" int neat_forward_lanes_steps(const void *lanes_dev, int32_t pop, neat
         for (int st = 0; st < steps && rc == NEAT_OK; ++st) {
             LanesArgs as = a;
             as.x = inputs_dev ? inputs_dev + (size_t)st * in_step_stride : nullptr;
-            as.x_next = inputs_dev && st + 1 < steps ? inputs_dev + (size_t)(st + 1) * in_step_stride : nullptr;
             as.y = outputs_dev + (size_t)st * out_step_stride;
             rc = launch_lanes(as, warps, st > 0, c.cap_stream);   // the first step fully waits for prior work
         }
