@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
         v[(pin3 << lgT) + tid] = pt.y;
         v[(pin4 << lgT) + tid] = 1.0f;
         if (sum_only)
-            for (int p = first; p < n_nodes; ++p) eval_node_sum<false>(nodes[p], edges, v, p, lgT, tid);
+            for (int p = first; p < n_nodes; ++p) eval_node_sum_by_count<false>(nodes[p], edges, v, p, lgT, tid);
         else
             for (int p = first; p < n_nodes; ++p) eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid);
         const float w = v[(pout << lgT) + tid];

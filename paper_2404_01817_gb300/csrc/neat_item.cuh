@@ -138,6 +138,50 @@ __device__ __forceinline__ float partials_agg(const uint2 *__restrict__ e, uint3
     return agg_combine(AGG, agg_combine(AGG, q0, q1), agg_combine(AGG, q2, q3));
 }
 
+// The four partials of an aggregation AGG over exactly EC edges (EC known
+// at compile time), for one column, combined along the tree: straight-line
+// code with the operations of `partials` in the same order (partial i mod 4,
+// edges in increasing i, from the aggregation's identity), so the same bits.
+template <bool T1, uint32_t AGG, int EC>
+__device__ __forceinline__ float agg_edges_fixed(const uint2 *__restrict__ e, const float *__restrict__ v, int lgT,
+                                                 int col)
+{
+    const float id = agg_identity(AGG);
+    float q[4] = {id, id, id, id};
+#pragma unroll
+    for (int i = 0; i < EC; ++i) {
+        const uint2 t = e[i];
+        q[i & 3] = agg_step(AGG, q[i & 3], __uint_as_float(t.x), v[vslot<T1>(t.y, lgT, col)]);
+    }
+    return agg_combine(AGG, agg_combine(AGG, q[0], q[1]), agg_combine(AGG, q[2], q[3]));
+}
+
+// The aggregate of a node's ec edges for one column: one dispatch on ec
+// into straight-line code for up to 8 edges (instead of a loop test per
+// four edges and three remainder tests), the loop of `partials` beyond.
+// For callers whose warp is on one node (a tile row of 32 or more columns,
+// a CPPN's queries): lanes on different nodes would run the cases one after
+// another.
+template <bool T1, uint32_t AGG>
+__device__ __forceinline__ float agg_edges(const uint2 *__restrict__ e, uint32_t ec, const float *__restrict__ v,
+                                           int lgT, int col)
+{
+    switch (ec) {
+    case 0: return agg_edges_fixed<T1, AGG, 0>(e, v, lgT, col);
+    case 1: return agg_edges_fixed<T1, AGG, 1>(e, v, lgT, col);
+    case 2: return agg_edges_fixed<T1, AGG, 2>(e, v, lgT, col);
+    case 3: return agg_edges_fixed<T1, AGG, 3>(e, v, lgT, col);
+    case 4: return agg_edges_fixed<T1, AGG, 4>(e, v, lgT, col);
+    case 5: return agg_edges_fixed<T1, AGG, 5>(e, v, lgT, col);
+    case 6: return agg_edges_fixed<T1, AGG, 6>(e, v, lgT, col);
+    case 7: return agg_edges_fixed<T1, AGG, 7>(e, v, lgT, col);
+    case 8: return agg_edges_fixed<T1, AGG, 8>(e, v, lgT, col);
+    default:
+        if (T1) return partials<T1, AGG == kAggSum>(AGG, e, ec, v, lgT, col, 0, 4);
+        return partials_agg<AGG>(e, ec, v, lgT, col);
+    }
+}
+
 // One whole node for one column of a tile (one thread), the aggregation
 // dispatched once per node: the threads of a node row take the same branch.
 template <bool FAST>
@@ -150,11 +194,32 @@ __device__ __forceinline__ void eval_node_tile(const uint4 ne, const uint2 *__re
     const uint32_t ec = ne.z >> 16;
     const uint2 *e = edges + (ne.z & 0xffffu);
     float a;
-    if (FAST || agg == kAggSum || agg == kAggMean) a = partials_agg<kAggSum>(e, ec, v, lgT, col);
-    else if (agg == kAggProduct) a = partials_agg<kAggProduct>(e, ec, v, lgT, col);
-    else a = partials_agg<kAggMax>(e, ec, v, lgT, col);
+    if (lgT >= 5) {
+        // a tile row fills whole warps: every lane of a warp is on this node,
+        // so the dispatch on its edge count does not diverge
+        if (FAST || agg == kAggSum || agg == kAggMean) a = agg_edges<false, kAggSum>(e, ec, v, lgT, col);
+        else if (agg == kAggProduct) a = agg_edges<false, kAggProduct>(e, ec, v, lgT, col);
+        else a = agg_edges<false, kAggMax>(e, ec, v, lgT, col);
+    } else {
+        if (FAST || agg == kAggSum || agg == kAggMean) a = partials_agg<kAggSum>(e, ec, v, lgT, col);
+        else if (agg == kAggProduct) a = partials_agg<kAggProduct>(e, ec, v, lgT, col);
+        else a = partials_agg<kAggMax>(e, ec, v, lgT, col);
+    }
     v[vslot<false>(p, lgT, col)] = FAST ? node_tanh(fmaf(__uint_as_float(ne.y), ec ? a : 0.0f, __uint_as_float(ne.x)))
                                         : node_output(ne, agg, act, ec, a);
+}
+
+// eval_node_sum with the edge sum dispatched on the edge count (the same
+// bits; with no edges the sum of the four +0 partials is already the +0 of
+// the empty set).  For callers whose warp is on one node.
+template <bool T1>
+__device__ __forceinline__ void eval_node_sum_by_count(const uint4 ne, const uint2 *__restrict__ edges,
+                                                       float *__restrict__ v, int p, int lgT, int col)
+{
+    const uint32_t act = ne.w & 0xffu;
+    if (act == kInputAct) return;
+    const float a = agg_edges<T1, kAggSum>(edges + (ne.z & 0xffffu), ne.z >> 16, v, lgT, col);
+    v[vslot<T1>(p, lgT, col)] = activate(act, fmaf(__uint_as_float(ne.y), a, __uint_as_float(ne.x)));
 }
 
 // One whole node for one column when every non-input node of the genome
