@@ -225,9 +225,12 @@ typedef struct neat_launch {
 
 /*
  * Genome order for the forward: genomes sorted by level count, deepest
- * first, into order_dev (int32 [pop], device).  Groups that share a warp then
- * walk similar numbers of levels.  Reads the record headers only; runs on
- * `stream` (one block).  The order changes speed, never results.
+ * first (counts above 63 share one bin), then by the number of non-input
+ * nodes, most first (64 bins over max_nodes), into order_dev (int32 [pop],
+ * device).  Groups that share a warp then walk similar numbers of levels and
+ * nodes; recurrent records (one level each) are ordered by node count.
+ * Reads the record headers only; runs on `stream` (one block).  The order
+ * changes speed, never results.
  */
 NEAT_API int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims d, int32_t *order_dev, void *stream);
 

@@ -555,32 +555,64 @@ extern "C" int neat_device_error(int32_t clear, uint32_t *out_host)
 namespace neat {
 namespace {
 
-// Counting sort of genomes by level count, deepest first (one block).
-__global__ void __launch_bounds__(1024) schedule_kernel(const uint8_t *rec, size_t stride, int pop, int32_t *order)
+// Sort key of a genome for the forward order: level count, deepest first
+// (counts above 63 share the first bin), then non-input nodes (the nodes
+// after the leading inputs, in units of 2^shift so that 64 bins span
+// max_nodes), most first.  Bin 0 comes first.  Recurrent records have one
+// level each, so only the node count orders them.
+constexpr int kSchedBins = 64 * 64;
+__device__ __forceinline__ int schedule_bin(const uint8_t *rec, int shift)
 {
-    __shared__ int hist[NEAT_MAX_NODES + 2];
-    for (int i = threadIdx.x; i < NEAT_MAX_NODES + 2; i += blockDim.x) hist[i] = 0;
+    const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(rec));
+    const uint32_t w3 = __ldg(reinterpret_cast<const uint32_t *>(rec) + 3);
+    const int n = (int)(w0 & 0xffffu), lv = min((int)(w0 >> 16), 63);
+    const int nonin = max(0, n - (int)min(w3 >> 16, (uint32_t)n));
+    return (63 - lv) * 64 + (63 - min(nonin >> shift, 63));
+}
+
+// Counting sort of genomes by schedule_bin (one block of 1024 threads): a
+// histogram, a block-wide exclusive scan (four bins per thread), placement.
+__global__ void __launch_bounds__(1024) schedule_kernel(const uint8_t *rec, size_t stride, int pop, int shift,
+                                                        int32_t *order)
+{
+    __shared__ int hist[kSchedBins];
+    __shared__ int warp_tot[32];
+    static_assert(kSchedBins == 4 * 1024, "four bins per thread");
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < kSchedBins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int g = threadIdx.x; g < pop; g += blockDim.x) {
-        const int lv = min((int)(__ldg(reinterpret_cast<const uint32_t *>(rec + (size_t)g * stride)) >> 16),
-                           NEAT_MAX_NODES);
-        atomicAdd(&hist[NEAT_MAX_NODES - lv], 1);
+    for (int g = tid; g < pop; g += blockDim.x) atomicAdd(&hist[schedule_bin(rec + (size_t)g * stride, shift)], 1);
+    __syncthreads();
+    // exclusive scan: each thread its four consecutive bins, then the warps
+    const int h0 = hist[4 * tid], h1 = hist[4 * tid + 1], h2 = hist[4 * tid + 2], h3 = hist[4 * tid + 3];
+    const int mine = h0 + h1 + h2 + h3;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
+    if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {                 // exclusive scan (deepest bin first)
-        int run = 0;
-        for (int i = 0; i < NEAT_MAX_NODES + 1; ++i) {
-            const int c = hist[i];
-            hist[i] = run;
-            run += c;
+    if (wid == 0) {
+        const int t = warp_tot[lane];
+        int wi = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
+        warp_tot[lane] = wi - t;           // exclusive: warps before this one
     }
     __syncthreads();
-    for (int g = threadIdx.x; g < pop; g += blockDim.x) {
-        const int lv = min((int)(__ldg(reinterpret_cast<const uint32_t *>(rec + (size_t)g * stride)) >> 16),
-                           NEAT_MAX_NODES);
-        order[atomicAdd(&hist[NEAT_MAX_NODES - lv], 1)] = g;
-    }
+    const int base = warp_tot[wid] + incl - mine;
+    hist[4 * tid] = base;
+    hist[4 * tid + 1] = base + h0;
+    hist[4 * tid + 2] = base + h0 + h1;
+    hist[4 * tid + 3] = base + h0 + h1 + h2;
+    __syncthreads();
+    for (int g = tid; g < pop; g += blockDim.x)
+        order[atomicAdd(&hist[schedule_bin(rec + (size_t)g * stride, shift)], 1)] = g;
 }
 
 }  // namespace
@@ -594,8 +626,10 @@ extern "C" int neat_schedule(const void *transformed_dev, int32_t pop, neat_dims
     if (pop < 0) return invalid("neat_schedule: pop < 0");
     if (pop == 0) return NEAT_OK;
     if (!transformed_dev || !order_dev) return invalid("neat_schedule: null pointer");
+    int shift = 0;
+    while ((d.max_nodes >> shift) > 64) ++shift;     // 64 node-count bins span max_nodes
     schedule_kernel<<<1, 1024, 0, as_stream(stream)>>>(static_cast<const uint8_t *>(transformed_dev),
-                                                       record_stride(d), pop, order_dev);
+                                                       record_stride(d), pop, shift, order_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_schedule: launch");
     return NEAT_OK;

@@ -281,6 +281,22 @@ def test_ant_full_size_sampled_steps(neat):
     print(f"ant full-size max scaled error {worst:.3g}")
 
 
+def _assert_node_count_tiebreak(rec, pop, d, o):
+    """Within a level count (up to 63), the order puts genomes with more
+    non-input nodes (the nodes after the leading inputs, in 64 bins over
+    max_nodes) first."""
+    hdr = rec.view(pop, -1)[:, :16].cpu().numpy().view(np.uint32)
+    n = (hdr[:, 0] & 0xFFFF).astype(np.int64)
+    lv = np.minimum(hdr[:, 0] >> 16, 63).astype(np.int64)
+    lead = np.minimum(hdr[:, 3] >> 16, n).astype(np.int64)
+    shift = 0
+    while (d.max_nodes >> shift) > 64:
+        shift += 1
+    nb = np.minimum((n - lead) >> shift, 63)
+    key = lv * 64 + nb
+    assert np.all(np.diff(key[o]) <= 0), "order is not (levels, non-input nodes) descending"
+
+
 def test_schedule_order_is_a_permutation_and_changes_nothing(neat):
     import torch
     for pop, B in [(W.ant_population(8, 2000), 1), (W.batched_populations(8, pop=100)[3], 16)]:
@@ -291,6 +307,7 @@ def test_schedule_order_is_a_permutation_and_changes_nothing(neat):
         assert sorted(o.tolist()) == list(range(pop.pop))
         dec = _decode(neat, rec, pop.pop, d)
         assert np.all(np.diff(dec.n_levels[o]) <= 0)            # deepest first
+        _assert_node_count_tiebreak(rec, pop.pop, d, o)
         x = _dev(W.normal_inputs(9, (pop.pop, B, pop.num_inputs)))
         L0 = neat.neat_default_launch(pop.pop, d, B)
         y0 = neat.neat_forward(rec, pop.pop, d, x, launch=L0).cpu().numpy()

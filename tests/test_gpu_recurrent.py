@@ -275,3 +275,27 @@ def test_recurrent_launch_shapes_bit_identical(neat):
         np.testing.assert_array_equal(y, ref, err_msg=f"G={G} tile={T} gpb={gpb} pdl={pdl}")
         n += 1
     assert n == 11
+
+
+def test_recurrent_schedule_order_by_node_count(neat):
+    """neat_schedule on recurrent records (one level each) orders genomes by
+    non-input node count, most first; the launch bench.py times (8 threads
+    per genome, 16 genomes per block, that order) gives the bits of the
+    default launch."""
+    import torch
+    pop = W.ant_recurrent_population(3, 3000)
+    d = _dims(neat, pop)
+    rec, _ = neat.neat_transform_recurrent(_dev(pop.nodes), _dev(pop.conns), d)
+    order = neat.neat_schedule(rec, 3000, d)
+    torch.cuda.synchronize()
+    o = order.cpu().numpy()
+    assert sorted(o.tolist()) == list(range(3000))
+    nonin = np.sum(~np.isnan(pop.nodes[:, :, 0]), axis=1) - 27
+    assert np.all(np.diff(nonin[o]) <= 0)
+    x = _dev(W.normal_inputs(31, (3000, 1, 27)))
+    ref = neat.neat_forward_recurrent(rec, 3000, d, x, 8).cpu().numpy()
+    L = neat.neat_default_launch_recurrent(3000, d, 1)
+    L.group, L.groups_per_block, L.pdl = 8, 16, 1
+    L.order_dev = order.data_ptr()
+    y = neat.neat_forward_recurrent(rec, 3000, d, x, 8, launch=L).cpu().numpy()
+    np.testing.assert_array_equal(y, ref)
