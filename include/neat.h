@@ -282,21 +282,30 @@ NEAT_API int neat_forward_fused(const void *transformed_dev, int32_t pop, neat_d
  *
  * The calculation of Section 3.3 for ONE input vector per genome per call
  * (a control loop that steps every genome once per environment step),
- * compiled per transformed population into lane programs: one thread
- * evaluates one genome and the 32 genomes of a warp share one instruction
- * stream, with no barrier anywhere in the walk.  neat_lanes_pack compiles
- * (once per transform); neat_forward_lanes / neat_forward_lanes_steps run.
- * Outputs are bit-identical to neat_forward with batch 1 (same node rule,
- * same aggregation order; the padding edges of a lane program change no
- * bit of any partial).  Limits: max_nodes <= 128; records from
- * neat_transform (feedforward; a genome whose record has no topological
- * order gets NaN outputs and is counted in neat_lanes_info.unordered).
+ * compiled per transformed population into lane programs: two threads
+ * ("lanes") evaluate one genome, one node each per "beat", and the 16
+ * genomes of a warp share one instruction stream, with one warp barrier per
+ * beat.  neat_lanes_pack compiles (once per transform); neat_forward_lanes /
+ * neat_forward_lanes_steps run.  Outputs are bit-identical to neat_forward
+ * with batch 1 (same node rule, same aggregation order; the padding edges
+ * of a lane program change no bit of any partial).  Limits: max_nodes <=
+ * 128; records from neat_transform (feedforward; a genome whose record has
+ * no topological order gets NaN outputs and is counted in
+ * neat_lanes_info.unordered).
  *
- * Compilation: per genome a list schedule of "beats" of up to two nodes
- * whose sources are all computed in earlier beats (longest remaining path
- * first); genomes sorted by (beats, edge quads), deepest first, 32 to a
- * warp; each warp program holds its beats' node entries and the nodes'
- * incoming edges in quads of four, interleaved by lane.
+ * Compilation: per genome a list schedule of beats of up to two nodes whose
+ * sources are all computed in earlier beats (longest remaining path first);
+ * genomes sorted by (beats, edge quads), deepest first, 16 to a warp; each
+ * warp program holds its beats' node entries and the nodes' incoming edges
+ * in quads of four, interleaved by lane.
+ *
+ * Recurrent networks (records of neat_transform_recurrent) compile with
+ * neat_lanes_pack_recurrent and run with neat_forward_lanes_recurrent: every
+ * non-input node is evaluated once per iteration from the previous
+ * iteration's values, so a genome's nodes are simply dealt to its two lanes
+ * by edge count (most first); each iteration runs the beats from one value
+ * tile into the other with one warp barrier.  A buffer packed for one
+ * forward gives NaN outputs in the other.
  */
 typedef struct neat_lanes_info {
     int32_t pop;
@@ -304,7 +313,7 @@ typedef struct neat_lanes_info {
     uint32_t max_warp_bytes;    /* largest warp program: a stage_bytes that stages every program */
     uint32_t warp_stride;       /* bytes reserved for each warp program */
     uint32_t unordered;         /* genomes with no feedforward order (NaN outputs) */
-    uint32_t reserved;
+    uint32_t recurrent;         /* 1: packed by neat_lanes_pack_recurrent */
 } neat_lanes_info;
 
 /* Bytes of the lanes buffer for `pop` genomes (0 if the dims are invalid or
@@ -349,6 +358,30 @@ NEAT_API int neat_forward_lanes_steps(const void *lanes_dev, int32_t pop, neat_d
                                       int64_t in_step_stride, float *outputs_dev, int64_t out_step_stride,
                                       int32_t steps, uint32_t stage_bytes, neat_lanes_cache **cache, void *stream);
 NEAT_API void neat_lanes_cache_destroy(neat_lanes_cache *cache);
+
+/* Recurrent lane programs (Section 3.3 names recurrent networks beside
+ * feedforward ones; the iteration rule is that of neat_forward_recurrent):
+ * as neat_lanes_pack, for records of neat_transform_recurrent (cycles and
+ * self-loops allowed), into a buffer of >= neat_lanes_bytes(pop, d) bytes.
+ * Errors as neat_lanes_pack. */
+NEAT_API int neat_lanes_pack_recurrent(const void *transformed_dev, int32_t pop, neat_dims d, void *lanes_dev,
+                                       size_t lanes_bytes, void *stream);
+
+/* `iterations` synchronous iterations of recurrent lane programs for one
+ * input vector per genome: inputs f32 [pop][I] -> outputs f32 [pop][O]
+ * (genome order), bit-identical to neat_forward_recurrent with batch 1 and
+ * the same records: non-input nodes start at 0, iteration k computes every
+ * non-input node from iteration k-1's values, the outputs are the values
+ * after the last iteration (0 for non-input outputs when iterations is 0).
+ * stage_bytes as for neat_forward_lanes (0: the smaller of warp_stride and
+ * 48 KB); pdl = 1 launches with programmatic dependent launch (the programs
+ * are staged while the previous kernel in the stream drains; the inputs
+ * are read after it completes).  NaN outputs for genomes with an error bit
+ * and for a buffer packed by neat_lanes_pack.  Errors: NEAT_EINVAL
+ * (iterations < 0, dims, stage_bytes), NEAT_ECUDA. */
+NEAT_API int neat_forward_lanes_recurrent(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                          int32_t iterations, float *outputs_dev, uint32_t stage_bytes, int32_t pdl,
+                                          void *stream);
 
 /* Picks stage_bytes for neat_forward_lanes_steps on this population and
  * device: one candidate per number of blocks an SM holds (the smallest

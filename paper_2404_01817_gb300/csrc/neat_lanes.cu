@@ -71,6 +71,7 @@ constexpr uint32_t kLaneBar = 16;                      // forward's shared memor
 constexpr uint32_t kLaneError = 1u;                    // genome has an error bit: outputs NaN
 constexpr uint32_t kLaneUnordered = 2u;                // no feedforward schedule (cyclic record): outputs NaN
 constexpr uint32_t kWarpFast = 1u;                     // every genome of the warp is sum + tanh
+constexpr uint32_t kWarpRecurrent = 2u;                // a recurrent program (neat_lanes_pack_recurrent)
 constexpr uint32_t kMeasError = 1u, kMeasUnordered = 2u;
 
 // Device header of a packed buffer.
@@ -81,7 +82,8 @@ struct LanesHeader {
     uint64_t warp_base, warp_stride;
     int32_t I, O, N, C;
     uint32_t unordered;      // genomes without a feedforward schedule
-    uint32_t pad[51];
+    uint32_t recurrent;      // 1: packed by neat_lanes_pack_recurrent
+    uint32_t pad[50];
 };
 static_assert(sizeof(LanesHeader) == kLanesHeaderBytes, "lanes header size");
 
@@ -139,21 +141,21 @@ constexpr int kSchedWarps = 4;
 // schedule positions and the genome's scratch image; mbarriers first.
 __host__ __device__ inline uint32_t sched_warp_bytes(uint32_t rec_bytes, int N, uint32_t scr_stride)
 {
-    return rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N) + scr_stride;
+    return rec_bytes + align16(4u * (uint32_t)kLaneMaxNodes + (uint32_t)N) + scr_stride;
 }
 
 __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uint8_t *rec, size_t stride, int pop,
                                                                       int I, int O, int N, uint32_t rec_bytes,
                                                                       uint8_t *lanes, LanesGeom geo,
-                                                                      const LanesHeader hv)
+                                                                      const LanesHeader hv, int recurrent)
 {
     uint8_t *sm = lane_sm;
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t per_warp = sched_warp_bytes(rec_bytes, N, (uint32_t)geo.scr_stride);
     uint8_t *srec = sm + 128 + (size_t)wi * per_warp;
-    uint32_t *hgt = reinterpret_cast<uint32_t *>(srec + rec_bytes);
-    uint8_t *sbv = reinterpret_cast<uint8_t *>(hgt + N);
-    uint8_t *scr = srec + rec_bytes + align16(4u * (uint32_t)N + (uint32_t)N);   // the scratch image
+    uint32_t *hgt = reinterpret_cast<uint32_t *>(srec + rec_bytes);            // kLaneMaxNodes words
+    uint8_t *sbv = reinterpret_cast<uint8_t *>(hgt + kLaneMaxNodes);
+    uint8_t *scr = srec + rec_bytes + align16(4u * (uint32_t)kLaneMaxNodes + (uint32_t)N);   // the scratch image
     const uint32_t bar = smem_addr(sm) + 8u * (uint32_t)wi;
     if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<LanesHeader *>(lanes) = hv;
     const int g = blockIdx.x * kSchedWarps + wi;
@@ -209,96 +211,145 @@ __global__ void __launch_bounds__(32 * kSchedWarps) lanes_sched_kernel(const uin
         hidden_before += __popc(m);
     }
 
-    // heights (longest path to a sink): a node's successors lie in higher levels
-    for (int p = lane; p < n; p += 32) {
-        hgt[p] = 0;
-        sbv[p] = (nodes[p].w & 0xffu) == kInputAct ? 0xfeu : 0xffu;
-    }
+    for (int p = lane; p < n; p += 32) sbv[p] = (nodes[p].w & 0xffu) == kInputAct ? 0xfeu : 0xffu;
     __syncwarp();
-    for (int L = nl - 1; L >= 1; --L) {
-        for (int p = lev[L] + lane; p < lev[L + 1]; p += 32) {
-            const uint4 ne = nodes[p];
-            if ((ne.w & 0xffu) == kInputAct) continue;
-            const uint32_t h = hgt[p] + 1u;
-            const int eb = (int)(ne.z & 0xffffu), ec = (int)(ne.z >> 16);
-            for (int e = 0; e < ec; ++e) atomicMax(&hgt[edges[eb + e].y], h);
-        }
-        __syncwarp();
-    }
-
-    // list schedule: each beat the kLaneG ready nodes of largest (height, -position)
-    int remaining = 0;
-    for (int p = lane; p < n; p += 32) remaining += sbv[p] == 0xffu;
-    remaining = __reduce_add_sync(0xffffffffu, remaining);
     uint32_t lane_quads[kLaneG];
     for (int k = 0; k < kLaneG; ++k) lane_quads[k] = 0;
     int b = 0;
     bool stuck = false;
-    for (; remaining > 0; ++b) {
-        uint32_t cand[kLaneMaxNodes / 32];
-#pragma unroll
-        for (int c = 0; c < kLaneMaxNodes / 32; ++c) {
-            const int p = lane + 32 * c;
-            cand[c] = 0;
-            if (p < n && sbv[p] == 0xffu) {
-                const uint32_t z = nodes[p].z;
-                const int eb = (int)(z & 0xffffu), ec = (int)(z >> 16);
-                bool ready = true;
-                for (int e = 0; e < ec && ready; ++e) {
-                    const uint8_t s = sbv[edges[eb + e].y];
-                    ready = s == 0xfeu || s < (uint8_t)b;
-                }
-                if (ready) cand[c] = (min(hgt[p], 0x7fffu) + 1u) << 16 | (0xffffu - (uint32_t)p);
-            }
+    if (recurrent) {
+        // every non-input node is evaluated once per iteration from the
+        // previous iteration's values, so beats carry no dependences: the
+        // nodes by quad count, most first (then position), dealt in turn to
+        // the genome's lanes in a snake (0 1 1 0 0 1 ...), beat i / kLaneG
+        // holding nodes i .. i + kLaneG - 1 of that order
+        uint32_t *keys = hgt;                                  // kLaneMaxNodes sort keys
+        const unsigned FULLM = 0xffffffffu, below = (1u << lane) - 1u;
+        int m = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int p = base + lane;
+            const bool ev = p < n && sbv[p] == 0xffu;
+            const unsigned msk = __ballot_sync(FULLM, ev);
+            if (ev) keys[m + __popc(msk & below)] = ((nodes[p].z >> 16) + 3u) >> 2 << 16 | (0xffffu - (uint32_t)p);
+            m += __popc(msk);
         }
-        int pick[kLaneG], q[kLaneG], np = 0;
-        for (int k = 0; k < kLaneG; ++k) {
-            uint32_t best = 0;
-#pragma unroll
-            for (int c = 0; c < kLaneMaxNodes / 32; ++c) best = max(best, cand[c]);
-            best = __reduce_max_sync(0xffffffffu, best);
-            if (best == 0) break;
-            const int p = (int)(0xffffu - (best & 0xffffu));
-#pragma unroll
-            for (int c = 0; c < kLaneMaxNodes / 32; ++c)
-                if (cand[c] == best) cand[c] = 0;
-            pick[np] = p;
-            q[np] = (int)((nodes[p].z >> 16) + 3u) >> 2;
-            ++np;
-        }
-        if (np == 0 || b >= 0xfe || b >= N) {
-            stuck = true;
-            break;
-        }
-        // deal the picks to the lanes: largest first, each to the lane with
-        // the fewest quads so far (every lane computes the same assignment)
-        int slot_of[kLaneG];
-        bool used_lane[kLaneG];
-        for (int k = 0; k < kLaneG; ++k) used_lane[k] = false;
-        for (int i = 0; i < np; ++i) {
-            int bi = -1;
-            for (int k = 0; k < np; ++k)
-                if (!used_lane[k] && (bi < 0 || q[k] > q[bi])) bi = k;
-            used_lane[bi] = true;
-            int lk = -1;
-            for (int k = 0; k < kLaneG; ++k) {
-                bool taken = false;
-                for (int t = 0; t < i; ++t) taken |= slot_of[t] == k;
-                if (!taken && (lk < 0 || lane_quads[k] < lane_quads[lk])) lk = k;
-            }
-            slot_of[i] = lk;
-            lane_quads[lk] += (uint32_t)q[bi];
-            if (lane == 0) sched[b * kLaneG + lk] = (uint8_t)pick[bi];
-            if (lane == (pick[bi] & 31)) sbv[pick[bi]] = (uint8_t)b;
-        }
-        if (lane == 0)
-            for (int k = 0; k < kLaneG; ++k) {
-                bool taken = false;
-                for (int t = 0; t < np; ++t) taken |= slot_of[t] == k;
-                if (!taken) sched[b * kLaneG + k] = 0xffu;
-            }
-        remaining -= np;
+        int m2 = 1;
+        while (m2 < m) m2 <<= 1;
+        for (int i = m + lane; i < m2; i += 32) keys[i] = 0;
         __syncwarp();
+        for (int kk = 2; kk <= m2; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < m2; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint32_t x = keys[i], y = keys[ixj];
+                        if ((x < y) == ((i & kk) == 0)) {
+                            keys[i] = y;
+                            keys[ixj] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        b = (m + kLaneG - 1) / kLaneG;
+        for (int i = lane; i < b * kLaneG; i += 32) sched[i] = 0xffu;
+        __syncwarp();
+        uint32_t q_of[kLaneG];
+        for (int k = 0; k < kLaneG; ++k) q_of[k] = 0;
+        for (int i = lane; i < m; i += 32) {
+            const int beat = i / kLaneG, r = i % kLaneG;
+            const int k = (beat & 1) ? kLaneG - 1 - r : r;
+            const uint32_t key = keys[i];
+            sched[beat * kLaneG + k] = (uint8_t)(0xffffu - (key & 0xffffu));
+            q_of[k] += key >> 16;
+        }
+        for (int k = 0; k < kLaneG; ++k) lane_quads[k] = __reduce_add_sync(FULLM, q_of[k]);
+        __syncwarp();
+    } else {
+        // heights (longest path to a sink): a node's successors lie in higher levels
+        for (int p = lane; p < n; p += 32) hgt[p] = 0;
+        __syncwarp();
+        for (int L = nl - 1; L >= 1; --L) {
+            for (int p = lev[L] + lane; p < lev[L + 1]; p += 32) {
+                const uint4 ne = nodes[p];
+                if ((ne.w & 0xffu) == kInputAct) continue;
+                const uint32_t h = hgt[p] + 1u;
+                const int eb = (int)(ne.z & 0xffffu), ec = (int)(ne.z >> 16);
+                for (int e = 0; e < ec; ++e) atomicMax(&hgt[edges[eb + e].y], h);
+            }
+            __syncwarp();
+        }
+
+        // list schedule: each beat the kLaneG ready nodes of largest (height, -position)
+        int remaining = 0;
+        for (int p = lane; p < n; p += 32) remaining += sbv[p] == 0xffu;
+        remaining = __reduce_add_sync(0xffffffffu, remaining);
+        for (; remaining > 0; ++b) {
+            uint32_t cand[kLaneMaxNodes / 32];
+    #pragma unroll
+            for (int c = 0; c < kLaneMaxNodes / 32; ++c) {
+                const int p = lane + 32 * c;
+                cand[c] = 0;
+                if (p < n && sbv[p] == 0xffu) {
+                    const uint32_t z = nodes[p].z;
+                    const int eb = (int)(z & 0xffffu), ec = (int)(z >> 16);
+                    bool ready = true;
+                    for (int e = 0; e < ec && ready; ++e) {
+                        const uint8_t s = sbv[edges[eb + e].y];
+                        ready = s == 0xfeu || s < (uint8_t)b;
+                    }
+                    if (ready) cand[c] = (min(hgt[p], 0x7fffu) + 1u) << 16 | (0xffffu - (uint32_t)p);
+                }
+            }
+            int pick[kLaneG], q[kLaneG], np = 0;
+            for (int k = 0; k < kLaneG; ++k) {
+                uint32_t best = 0;
+    #pragma unroll
+                for (int c = 0; c < kLaneMaxNodes / 32; ++c) best = max(best, cand[c]);
+                best = __reduce_max_sync(0xffffffffu, best);
+                if (best == 0) break;
+                const int p = (int)(0xffffu - (best & 0xffffu));
+    #pragma unroll
+                for (int c = 0; c < kLaneMaxNodes / 32; ++c)
+                    if (cand[c] == best) cand[c] = 0;
+                pick[np] = p;
+                q[np] = (int)((nodes[p].z >> 16) + 3u) >> 2;
+                ++np;
+            }
+            if (np == 0 || b >= 0xfe || b >= N) {
+                stuck = true;
+                break;
+            }
+            // deal the picks to the lanes: largest first, each to the lane with
+            // the fewest quads so far (every lane computes the same assignment)
+            int slot_of[kLaneG];
+            bool used_lane[kLaneG];
+            for (int k = 0; k < kLaneG; ++k) used_lane[k] = false;
+            for (int i = 0; i < np; ++i) {
+                int bi = -1;
+                for (int k = 0; k < np; ++k)
+                    if (!used_lane[k] && (bi < 0 || q[k] > q[bi])) bi = k;
+                used_lane[bi] = true;
+                int lk = -1;
+                for (int k = 0; k < kLaneG; ++k) {
+                    bool taken = false;
+                    for (int t = 0; t < i; ++t) taken |= slot_of[t] == k;
+                    if (!taken && (lk < 0 || lane_quads[k] < lane_quads[lk])) lk = k;
+                }
+                slot_of[i] = lk;
+                lane_quads[lk] += (uint32_t)q[bi];
+                if (lane == 0) sched[b * kLaneG + lk] = (uint8_t)pick[bi];
+                if (lane == (pick[bi] & 31)) sbv[pick[bi]] = (uint8_t)b;
+            }
+            if (lane == 0)
+                for (int k = 0; k < kLaneG; ++k) {
+                    bool taken = false;
+                    for (int t = 0; t < np; ++t) taken |= slot_of[t] == k;
+                    if (!taken) sched[b * kLaneG + k] = 0xffu;
+                }
+            remaining -= np;
+            __syncwarp();
+        }
     }
     if (lane == 0) {
         uint32_t mq = 0;
@@ -390,9 +441,13 @@ __global__ void __launch_bounds__(1024) lanes_sort_kernel(uint8_t *lanes, LanesG
 
 // One warp per warp program: lane (j, k) = (lane % kLaneJ, lane / kLaneJ)
 // writes the stream of slot k of genome order[kLaneJ w + j].  The warp's
-// records and schedules are staged in shared memory first.
+// records and schedules are staged in shared memory first.  Value slots are
+// slot_bytes apart in the forward's tile (128: one tile; 256: the recurrent
+// forward's two tiles, interleaved by slot); warp_flags go into every warp
+// header.
 __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size_t stride, int pop, int I, int O,
-                                                        int N, uint32_t rec_bytes, uint8_t *lanes, LanesGeom geo)
+                                                        int N, uint32_t rec_bytes, uint8_t *lanes, LanesGeom geo,
+                                                        uint32_t slot_bytes, uint32_t warp_flags)
 {
     uint8_t *sm = lane_sm;
     const int lane = threadIdx.x;
@@ -459,13 +514,13 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
     const uint32_t bytes = off_rows + kRowBytes * (uint32_t)rows_w;
     if (lane == 0) {
         reinterpret_cast<uint4 *>(wp)[0] = make_uint4((uint32_t)nbw | ((uint32_t)rows_w << 16), bytes,
-                                                      fast_w ? kWarpFast : 0u, 0u);
+                                                      (fast_w ? kWarpFast : 0u) | warp_flags, 0u);
         atomicMax(&hdr->max_warp_bytes, bytes);
     }
     reinterpret_cast<int2 *>(wp + 16)[lane] = make_int2(g, (int)flags);
     const uint32_t col4 = 4u * (uint32_t)lane;
-    const uint32_t zero_off = (uint32_t)N * 128u + col4, one_off = (uint32_t)(N + 1) * 128u + col4;
-    const uint32_t junk_off = (uint32_t)(N + 2) * 128u + col4;
+    const uint32_t zero_off = (uint32_t)N * slot_bytes + col4, one_off = (uint32_t)(N + 1) * slot_bytes + col4;
+    const uint32_t junk_off = (uint32_t)(N + 2) * slot_bytes + col4;
     uint8_t *rows = wp + off_rows + 24u * (uint32_t)lane;
     // padding quads: rows 0 (sum, mean), 1 (product), 2 (max); row 0 alone in a fast warp
     {
@@ -491,7 +546,7 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
             const uint32_t act = ne.w & 0xffu, agg = (ne.w >> 8) & 0xffu;
             const uint32_t pad = agg == kAggProduct ? 1u : (agg == kAggMax ? 2u : 0u);
             q = (ec + 3u) >> 2;
-            ent = make_uint4(ne.x, ne.y, ((uint32_t)vslot[p] * 128u + col4) | (row << 16),
+            ent = make_uint4(ne.x, ne.y, ((uint32_t)vslot[p] * slot_bytes + col4) | (row << 16),
                              ec | (act << 16) | (agg << 24) | (pad << 28));
             const float pad_w = agg == kAggProduct ? 1.0f : (agg == kAggMax ? __int_as_float(0x7fc00000) : -0.0f);
             const uint32_t pad_s = agg == kAggProduct ? one_off : zero_off;
@@ -503,7 +558,7 @@ __global__ void __launch_bounds__(32) lanes_pack_kernel(const uint8_t *rec, size
                     if (e < ec) {
                         const uint2 ed = edges[eb + e];
                         wv[e4] = __uint_as_float(ed.x);
-                        so[e4] = (uint32_t)vslot[ed.y] * 128u + col4;
+                        so[e4] = (uint32_t)vslot[ed.y] * slot_bytes + col4;
                     } else {
                         wv[e4] = pad_w;
                         so[e4] = pad_s;
@@ -551,11 +606,11 @@ __device__ __forceinline__ float ldv(const char *V, uint32_t off) { return *rein
 // A node's value offset in every column of its genome: kLaneG stores, the
 // m-th into column (lane + m * kLaneJ) mod 32, so that the 32 lanes' m-th
 // stores hit 32 different banks.
-__device__ __forceinline__ void store_value(char *V, uint32_t dst, int lane, float v)
+__device__ __forceinline__ void store_value(char *V, uint32_t dst, int lane, float v, uint32_t wr = 0)
 {
 #pragma unroll
     for (int m = 0; m < kLaneG; ++m)
-        *reinterpret_cast<float *>(V + ((dst & ~127u) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2))) = v;
+        *reinterpret_cast<float *>(V + (((dst & ~127u) + wr) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2))) = v;
 }
 
 // The beats of a warp program at P (shared or device memory).  FAST: every
@@ -563,7 +618,12 @@ __device__ __forceinline__ void store_value(char *V, uint32_t dst, int lane, flo
 // trips (the beat's largest quad count), trip t reading the lane's quad t or
 // its padding quad; partials, node rule, the value into every column of the
 // genome, and a warp barrier.
-template <bool FAST>
+// RD / WR: byte offsets added to every value read / write (0 / 0 for the
+// feedforward tile; the recurrent forward reads one of its two interleaved
+// tiles and writes the other); SYNC: a warp barrier after every beat (the
+// feedforward walk reads values written in earlier beats; the recurrent
+// walk reads only the previous iteration's tile).
+template <bool FAST, uint32_t RD = 0, uint32_t WR = 0, bool SYNC = true>
 __device__ __forceinline__ void walk(const unsigned char *__restrict__ P, int nb, float *V, int lane)
 {
     const uint32_t off_node = kWarpSbOff + align16(4u * (uint32_t)nb);
@@ -589,8 +649,8 @@ __device__ __forceinline__ void walk(const unsigned char *__restrict__ P, int nb
             const uint2 w01 = *reinterpret_cast<const uint2 *>(q);
             const uint2 w23 = *reinterpret_cast<const uint2 *>(q + 8);
             const uint2 s = *reinterpret_cast<const uint2 *>(q + 16);
-            const float v0 = ldv(Vc, s.x & 0xffffu), v1 = ldv(Vc, s.x >> 16);
-            const float v2 = ldv(Vc, s.y & 0xffffu), v3 = ldv(Vc, s.y >> 16);
+            const float v0 = ldv(Vc, (s.x & 0xffffu) + RD), v1 = ldv(Vc, (s.x >> 16) + RD);
+            const float v2 = ldv(Vc, (s.y & 0xffffu) + RD), v3 = ldv(Vc, (s.y >> 16) + RD);
             if (FAST) {
                 p0 = fmaf(__uint_as_float(w01.x), v0, p0);
                 p1 = fmaf(__uint_as_float(w01.y), v1, p1);
@@ -610,8 +670,8 @@ __device__ __forceinline__ void walk(const unsigned char *__restrict__ P, int nb
             const float a = agg_combine(agg, agg_combine(agg, p0, p1), agg_combine(agg, p2, p3));
             v = node_output(ne, agg, (ne.w >> 16) & 0xffu, ec, a);
         }
-        store_value(Vw, ne.z & 0xffffu, lane, v);
-        __syncwarp();
+        store_value(Vw, ne.z & 0xffffu, lane, v, WR);
+        if (SYNC) __syncwarp();
     }
 }
 
@@ -647,10 +707,11 @@ __device__ __forceinline__ Quad lds_quad(uint32_t a)
 __device__ __forceinline__ float tile_ld(uint32_t off) { return *reinterpret_cast<const float *>(lane_sm + kLaneBar + off); }
 __device__ __forceinline__ void tile_st(uint32_t off, float v) { *reinterpret_cast<float *>(lane_sm + kLaneBar + off) = v; }
 
+template <uint32_t RD = 0>
 __device__ __forceinline__ void fma_quad(const Quad &q, float &p0, float &p1, float &p2, float &p3)
 {
-    const float v0 = tile_ld(q.s.x & 0xffffu), v1 = tile_ld(q.s.x >> 16);
-    const float v2 = tile_ld(q.s.y & 0xffffu), v3 = tile_ld(q.s.y >> 16);
+    const float v0 = tile_ld((q.s.x & 0xffffu) + RD), v1 = tile_ld((q.s.x >> 16) + RD);
+    const float v2 = tile_ld((q.s.y & 0xffffu) + RD), v3 = tile_ld((q.s.y >> 16) + RD);
     p0 = fmaf(__uint_as_float(q.w01.x), v0, p0);
     p1 = fmaf(__uint_as_float(q.w01.y), v1, p1);
     p2 = fmaf(__uint_as_float(q.w23.x), v2, p2);
@@ -684,7 +745,7 @@ __device__ __forceinline__ void load_beat_head(BeatState &st, uint4 ne, uint32_t
 // first rows) is loaded before the node rule, the store of the value into
 // every column of the genome and the warp barrier.  A lane past its own
 // quads reads the padding quad at `ra`.
-template <int T>
+template <int T, uint32_t RD = 0, uint32_t WR = 0, bool SYNC = true>
 __device__ __forceinline__ void run_beats(BeatState &st, int b, int len, int nb, uint32_t na, uint32_t ra, int lane)
 {
     for (int i = 0; i < len; ++i, ++b) {
@@ -697,19 +758,21 @@ __device__ __forceinline__ void run_beats(BeatState &st, int b, int len, int nb,
                 q[t] = t < kHeadRows ? st.q[t < kHeadRows ? t : 0]
                                      : lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
 #pragma unroll
-            for (int t = 0; t < T; ++t) fma_quad(q[t], p0, p1, p2, p3);
+            for (int t = 0; t < T; ++t) fma_quad<RD>(q[t], p0, p1, p2, p3);
         }
         const uint4 ne = st.ne;
         load_beat_head(st, nn, ra);
         const float v = node_tanh(fmaf(__uint_as_float(ne.y), (p0 + p1) + (p2 + p3), __uint_as_float(ne.x)));
         const uint32_t dst = ne.z & 0xffffu;
 #pragma unroll
-        for (int m = 0; m < kLaneG; ++m) tile_st((dst & ~127u) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2), v);
-        __syncwarp();
+        for (int m = 0; m < kLaneG; ++m)
+            tile_st(((dst & ~127u) + WR) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2), v);
+        if (SYNC) __syncwarp();
     }
 }
 
 // The same for any even T above 8 (trip pairs in a loop after the head rows).
+template <uint32_t RD = 0, uint32_t WR = 0, bool SYNC = true>
 __device__ __forceinline__ void run_beats_any(BeatState &st, int T, int b, int len, int nb, uint32_t na, uint32_t ra,
                                            int lane)
 {
@@ -718,20 +781,21 @@ __device__ __forceinline__ void run_beats_any(BeatState &st, int T, int b, int l
         float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
 #pragma unroll
         for (int t = 0; t < kHeadRows; ++t)
-            if (t < T) fma_quad(st.q[t], p0, p1, p2, p3);
+            if (t < T) fma_quad<RD>(st.q[t], p0, p1, p2, p3);
         for (int t = kHeadRows; t < T; t += 2) {
             const Quad qa = lds_quad((uint32_t)t < st.mt ? st.base + (uint32_t)t * kRowBytes : ra);
             const Quad qb = lds_quad((uint32_t)t + 1u < st.mt ? st.base + (uint32_t)(t + 1) * kRowBytes : ra);
-            fma_quad(qa, p0, p1, p2, p3);
-            fma_quad(qb, p0, p1, p2, p3);
+            fma_quad<RD>(qa, p0, p1, p2, p3);
+            fma_quad<RD>(qb, p0, p1, p2, p3);
         }
         const uint4 ne = st.ne;
         load_beat_head(st, nn, ra);
         const float v = node_tanh(fmaf(__uint_as_float(ne.y), (p0 + p1) + (p2 + p3), __uint_as_float(ne.x)));
         const uint32_t dst = ne.z & 0xffffu;
 #pragma unroll
-        for (int m = 0; m < kLaneG; ++m) tile_st((dst & ~127u) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2), v);
-        __syncwarp();
+        for (int m = 0; m < kLaneG; ++m)
+            tile_st(((dst & ~127u) + WR) | ((uint32_t)((lane + m * kLaneJ) & 31) << 2), v);
+        if (SYNC) __syncwarp();
     }
 }
 
@@ -740,6 +804,7 @@ __device__ __forceinline__ void run_beats_any(BeatState &st, int T, int b, int l
 // per run to a loop compiled for that count (one code path per loop keeps
 // the hot loop compact; dispatching per beat measured ~120 cycles slower
 // per beat).
+template <uint32_t RD = 0, uint32_t WR = 0, bool SYNC = true>
 __device__ __forceinline__ void walk_fast_staged(uint32_t P, int nb, int lane)
 {
     const uint32_t off_node = kWarpSbOff + align16(4u * (uint32_t)nb);
@@ -753,12 +818,12 @@ __device__ __forceinline__ void walk_fast_staged(uint32_t P, int nb, int lane)
         const uint32_t e = lds_u32(sa + 4u * (uint32_t)b);
         const int T = (int)(e & 0xffffu), len = max(1, (int)(e >> 16));
         switch (T) {
-        case 0: run_beats<0>(st, b, len, nb, na, ra, lane); break;
-        case 2: run_beats<2>(st, b, len, nb, na, ra, lane); break;
-        case 4: run_beats<4>(st, b, len, nb, na, ra, lane); break;
-        case 6: run_beats<6>(st, b, len, nb, na, ra, lane); break;
-        case 8: run_beats<8>(st, b, len, nb, na, ra, lane); break;
-        default: run_beats_any(st, T, b, len, nb, na, ra, lane);
+        case 0: run_beats<0, RD, WR, SYNC>(st, b, len, nb, na, ra, lane); break;
+        case 2: run_beats<2, RD, WR, SYNC>(st, b, len, nb, na, ra, lane); break;
+        case 4: run_beats<4, RD, WR, SYNC>(st, b, len, nb, na, ra, lane); break;
+        case 6: run_beats<6, RD, WR, SYNC>(st, b, len, nb, na, ra, lane); break;
+        case 8: run_beats<8, RD, WR, SYNC>(st, b, len, nb, na, ra, lane); break;
+        default: run_beats_any<RD, WR, SYNC>(st, T, b, len, nb, na, ra, lane);
         }
         b += len;
     }
@@ -774,7 +839,10 @@ constexpr int kLaneInputChunks = 4;
 // instead of one per genome and float); each lane stores the words of its
 // chunks into its own column and its partner's.  A chunk that reaches
 // outside the input array [x, x_end) is read word by word, the row's words
-// only.  Lanes without a genome store zeros.
+// only.  Lanes without a genome store zeros.  SS: floats between value
+// slots (32; 64 for the recurrent forward's two interleaved tiles, TWO: the
+// inputs go into both).
+template <int SS = 32, bool TWO = false>
 __device__ __forceinline__ void load_inputs(const float *__restrict__ x, const float *x_end, int g, int I, int lane,
                                             float *V)
 {
@@ -814,8 +882,12 @@ __device__ __forceinline__ void load_inputs(const float *__restrict__ x, const f
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (j + q >= 0 && j + q < I) {
-                    V[(j + q) * 32 + lane] = e[q];
-                    V[(j + q) * 32 + mate] = e[q];
+                    V[(j + q) * SS + lane] = e[q];
+                    V[(j + q) * SS + mate] = e[q];
+                    if (TWO) {
+                        V[(j + q) * SS + 32 + lane] = e[q];
+                        V[(j + q) * SS + 32 + mate] = e[q];
+                    }
                 }
         }
     }
@@ -870,6 +942,7 @@ __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
         }
     }
     const int nb = (int)(wh.x & 0xffffu);
+    if (wh.z & kWarpRecurrent) ok = false;   // packed for the recurrent forward: its offsets index two tiles
     if (ok) {
         const bool fast = (wh.z & kWarpFast) != 0;
         if (staged) {
@@ -894,6 +967,100 @@ __global__ void __launch_bounds__(32) lanes_kernel(const LanesArgs a)
         } else {
             for (int j = lane / kLaneJ; j < a.O; j += kLaneG) yg[j] = nan_out ? qnan : V[(a.I + j) * 32 + lane];
         }
+    }
+}
+
+// ------------------------------------------------------ recurrent forward
+
+// Shared memory of the recurrent forward: [0, 16) mbarrier | two value
+// tiles interleaved by slot, (N + 3) x 256 bytes (slot s of tile 0 at
+// 256 s, of tile 1 at 256 s + 128) | program (cap bytes).
+__host__ __device__ inline uint32_t lanes_rnn_tile_bytes(int N) { return (uint32_t)(N + 3) * 256u; }
+
+// One iteration of a recurrent warp program: every beat reads tile RD and
+// writes tile WR (byte offsets 0 / 128), no barrier between beats.
+template <uint32_t RD, uint32_t WR>
+__device__ __forceinline__ void rnn_iteration(const unsigned char *sprog, const unsigned char *gw, bool staged,
+                                              bool fast, int nb, float *V, int lane)
+{
+    if (staged) {
+        if (fast) walk_fast_staged<RD, WR, false>(smem_addr(sprog), nb, lane);
+        else walk<false, RD, WR, false>(sprog, nb, V, lane);
+    } else {
+        if (fast) walk<true, RD, WR, false>(gw, nb, V, lane);
+        else walk<false, RD, WR, false>(gw, nb, V, lane);
+    }
+    __syncwarp();      // the iteration's writes before the next one reads them
+}
+
+// K synchronous iterations of recurrent lane programs (records of
+// neat_transform_recurrent packed by neat_lanes_pack_recurrent), one input
+// vector per genome: non-input nodes start at 0; iteration k computes every
+// non-input node from iteration k-1's values (tile k mod 2 -> tile (k+1)
+// mod 2); the outputs are read from tile K mod 2.  Staging, inputs and
+// error handling as in lanes_kernel.
+template <bool PDL>
+__global__ void __launch_bounds__(32) lanes_rnn_kernel(const LanesArgs a, int K)
+{
+    unsigned char *sm = lane_sm;
+    float *V = reinterpret_cast<float *>(sm + kLaneBar);
+    unsigned char *sprog = sm + kLaneBar + lanes_rnn_tile_bytes(a.N);
+    const int lane = threadIdx.x;
+    const unsigned char *gw = a.lanes + a.warp_base + (size_t)blockIdx.x * a.warp_stride;
+    const uint4 wh = __ldg(reinterpret_cast<const uint4 *>(gw));
+    const int2 li = __ldg(reinterpret_cast<const int2 *>(gw + 16) + lane);
+    const uint32_t bytes = wh.y;
+    const bool staged = bytes <= a.cap;
+    const uint32_t bar = smem_addr(sm);
+    if (staged && lane == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(sprog), gw, bytes, bar);
+    }
+    const int g = li.x;
+    // both tiles zero (non-input nodes start at 0; the zero slots), the one
+    // slots 1; tiles are block-private, so this overlaps the previous kernel
+    for (int i = lane; i < (a.N + 3) * 64; i += 32) V[i] = 0.0f;
+    V[(a.N + 1) * 64 + lane] = 1.0f;
+    V[(a.N + 1) * 64 + 32 + lane] = 1.0f;
+    if constexpr (PDL) {
+        if (g >= 0 && a.I > 0 && lane < kLaneJ) {
+            const char *p0 = reinterpret_cast<const char *>(a.x + (size_t)g * a.I);
+            const char *p1 = p0 + 4u * (uint32_t)a.I - 1;
+            for (const char *p = p0; p <= p1; p += 128) prefetch_l2(p);
+            prefetch_l2(p1);
+        }
+        pdl_wait();
+        pdl_trigger();
+    }
+    __syncwarp();
+    load_inputs<64, true>(a.x, a.x + (size_t)a.pop * a.I, g, a.I, lane, V);
+    bool ok = true;
+    if (staged) {
+        __syncwarp();
+        ok = __all_sync(0xffffffffu, mbar_wait(bar, 0));
+        if (!ok) {
+            if (lane == 0) atomicOr(&g_lanes_error, kErrWaitExpired);
+            mbar_wait(bar, 0);
+        }
+    }
+    __syncwarp();
+    const int nb = (int)(wh.x & 0xffffu);
+    if (!(wh.z & kWarpRecurrent)) ok = false;   // a feedforward program: its offsets index one tile
+    if (ok) {
+        const bool fast = (wh.z & kWarpFast) != 0;
+        for (int k = 0; k + 1 < K; k += 2) {
+            rnn_iteration<0u, 128u>(sprog, gw, staged, fast, nb, V, lane);
+            rnn_iteration<128u, 0u>(sprog, gw, staged, fast, nb, V, lane);
+        }
+        if (K & 1) rnn_iteration<0u, 128u>(sprog, gw, staged, fast, nb, V, lane);
+    }
+    if (g >= 0) {
+        float *yg = a.y + (size_t)g * a.O;
+        const bool nan_out = !ok || (li.y & (int)(kLaneError | kLaneUnordered));
+        const float qnan = __int_as_float(0x7fc00000);
+        const int fin = (K & 1) ? 32 : 0;
+        for (int j = lane / kLaneJ; j < a.O; j += kLaneG) yg[j] = nan_out ? qnan : V[(a.I + j) * 64 + fin + lane];
     }
 }
 
@@ -927,7 +1094,7 @@ int launch_lanes(const LanesArgs &a, int warps, bool pdl, cudaStream_t s)
 }
 
 int make_lanes_args(const void *lanes, int32_t pop, const neat_dims &d, const float *x, float *y, uint32_t cap,
-                    LanesArgs *out, int *warps)
+                    LanesArgs *out, int *warps, bool recurrent = false)
 {
     if (!lanes_dims_ok(d))
         return invalid("neat_forward_lanes: invalid dims (lane programs need max_nodes <= 128 and records <= 12 KB)");
@@ -946,11 +1113,40 @@ int make_lanes_args(const void *lanes, int32_t pop, const neat_dims &d, const fl
     a.O = d.num_outputs;
     a.N = d.max_nodes;
     a.cap = cap ? align16(std::min<uint32_t>(cap, (uint32_t)g.warp_stride)) : default_cap(g);
-    if (kLaneBar + lanes_tile_bytes(a.N) + a.cap > kMaxSmemPerBlock) return invalid("neat_forward_lanes: stage_bytes too large");
+    const uint32_t tile = recurrent ? lanes_rnn_tile_bytes(a.N) : lanes_tile_bytes(a.N);
+    if (kLaneBar + tile + a.cap > kMaxSmemPerBlock) return invalid("neat_forward_lanes: stage_bytes too large");
     *out = a;
     *warps = g.warps;
     return NEAT_OK;
 }
+
+int launch_lanes_rnn(const LanesArgs &a, int warps, int K, bool pdl, cudaStream_t s)
+{
+    if (warps == 0) return NEAT_OK;
+    const size_t smem = kLaneBar + lanes_rnn_tile_bytes(a.N) + a.cap;
+    auto f = pdl ? lanes_rnn_kernel<true> : lanes_rnn_kernel<false>;
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(f), smem,
+                                "neat_forward_lanes_recurrent: shared memory per block");
+    if (rc) return rc;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)warps);
+    cfg.blockDim = dim3(32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, f, a, K);
+    if (e != cudaSuccess) return cuda_fail(e, "neat_forward_lanes_recurrent: launch");
+    return NEAT_OK;
+}
+
+int lanes_pack_impl(const void *transformed_dev, int32_t pop, neat_dims d, void *lanes_dev, size_t lanes_bytes,
+                    void *stream, int recurrent);
 
 }  // namespace
 }  // namespace neat
@@ -967,6 +1163,21 @@ extern "C" int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_di
                                size_t lanes_bytes, void *stream)
 {
     TraceRange trace_range("neat_lanes_pack");
+    return lanes_pack_impl(transformed_dev, pop, d, lanes_dev, lanes_bytes, stream, 0);
+}
+
+extern "C" int neat_lanes_pack_recurrent(const void *transformed_dev, int32_t pop, neat_dims d, void *lanes_dev,
+                                         size_t lanes_bytes, void *stream)
+{
+    TraceRange trace_range("neat_lanes_pack_recurrent");
+    return lanes_pack_impl(transformed_dev, pop, d, lanes_dev, lanes_bytes, stream, 1);
+}
+
+namespace neat {
+namespace {
+int lanes_pack_impl(const void *transformed_dev, int32_t pop, neat_dims d, void *lanes_dev, size_t lanes_bytes,
+                    void *stream, int recurrent)
+{
     clear_error();
     if (!lanes_dims_ok(d))
         return invalid("neat_lanes_pack: invalid dims (lane programs need max_nodes <= 128 and records <= 12 KB)");
@@ -991,6 +1202,7 @@ extern "C" int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_di
     h.O = d.num_outputs;
     h.N = d.max_nodes;
     h.C = d.max_conns;
+    h.recurrent = recurrent ? 1u : 0u;
     const uint8_t *rec = static_cast<const uint8_t *>(transformed_dev);
     const size_t stride = record_stride(d);
     const int N = d.max_nodes;
@@ -1004,7 +1216,7 @@ extern "C" int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_di
     if (rc) return rc;
     // the header goes in as a kernel argument (also when pop is 0)
     lanes_sched_kernel<<<std::max(1, (pop + kSchedWarps - 1) / kSchedWarps), 32 * kSchedWarps, sched_smem, s>>>(
-        rec, stride, pop, d.num_inputs, d.num_outputs, N, g.rec_bytes, L, g, h);
+        rec, stride, pop, d.num_inputs, d.num_outputs, N, g.rec_bytes, L, g, h, recurrent);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_lanes_pack: schedule");
     if (pop == 0) return NEAT_OK;
@@ -1012,10 +1224,26 @@ extern "C" int neat_lanes_pack(const void *transformed_dev, int32_t pop, neat_di
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_lanes_pack: sort");
     lanes_pack_kernel<<<g.warps, 32, pack_smem, s>>>(rec, stride, pop, d.num_inputs, d.num_outputs, N, g.rec_bytes, L,
-                                                     g);
+                                                     g, recurrent ? 256u : 128u, recurrent ? kWarpRecurrent : 0u);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_lanes_pack: pack");
     return NEAT_OK;
+}
+}  // namespace
+}  // namespace neat
+
+extern "C" int neat_forward_lanes_recurrent(const void *lanes_dev, int32_t pop, neat_dims d, const float *inputs_dev,
+                                            int32_t iterations, float *outputs_dev, uint32_t stage_bytes, int32_t pdl,
+                                            void *stream)
+{
+    TraceRange trace_range("neat_forward_lanes_recurrent");
+    clear_error();
+    if (iterations < 0) return invalid("neat_forward_lanes_recurrent: iterations < 0");
+    LanesArgs a;
+    int warps = 0;
+    int rc = make_lanes_args(lanes_dev, pop, d, inputs_dev, outputs_dev, stage_bytes, &a, &warps, true);
+    if (rc) return rc;
+    return launch_lanes_rnn(a, warps, iterations, pdl != 0, as_stream(stream));
 }
 
 extern "C" int neat_lanes_query(const void *lanes_dev, neat_lanes_info *out_host)
@@ -1031,7 +1259,7 @@ extern "C" int neat_lanes_query(const void *lanes_dev, neat_lanes_info *out_host
     out_host->max_warp_bytes = h.max_warp_bytes;
     out_host->warp_stride = (uint32_t)h.warp_stride;
     out_host->unordered = h.unordered;
-    out_host->reserved = 0;
+    out_host->recurrent = h.recurrent;
     return NEAT_OK;
 }
 

@@ -122,7 +122,7 @@ def mutation(**kw) -> Mutation:
 
 class LanesInfo(ctypes.Structure):
     _fields_ = [("pop", _i32), ("warps", _i32), ("max_warp_bytes", ctypes.c_uint32),
-                ("warp_stride", ctypes.c_uint32), ("unordered", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("warp_stride", ctypes.c_uint32), ("unordered", ctypes.c_uint32), ("recurrent", ctypes.c_uint32)]
 
 
 class PlanOptions(ctypes.Structure):
@@ -159,6 +159,8 @@ _sig = {
     "neat_lanes_pack": (ctypes.c_int, [_P, _i32, Dims, _P, ctypes.c_size_t, _P]),
     "neat_lanes_query": (ctypes.c_int, [_P, ctypes.POINTER(LanesInfo)]),
     "neat_forward_lanes": (ctypes.c_int, [_P, _i32, Dims, _P, _P, ctypes.c_uint32, _P]),
+    "neat_lanes_pack_recurrent": (ctypes.c_int, [_P, _i32, Dims, _P, ctypes.c_size_t, _P]),
+    "neat_forward_lanes_recurrent": (ctypes.c_int, [_P, _i32, Dims, _P, _i32, _P, ctypes.c_uint32, _i32, _P]),
     "neat_forward_lanes_steps": (ctypes.c_int, [_P, _i32, Dims, _P, _i64, _P, _i64, _i32, ctypes.c_uint32,
                                                 ctypes.POINTER(_P), _P]),
     "neat_lanes_cache_destroy": (None, [_P]),
@@ -502,7 +504,7 @@ def neat_lanes_bytes(pop: int, d: Dims) -> int:
 
 
 def neat_lanes_pack(transformed, pop: int, d: Dims, lanes=None, stream=None):
-    """Compile lane programs (one thread per genome) of a transformed
+    """Compile lane programs (two threads per genome) of a transformed
     population; returns the lanes buffer (uint8 CUDA tensor)."""
     import torch
     nbytes = neat_lanes_bytes(pop, d)
@@ -513,6 +515,34 @@ def neat_lanes_pack(transformed, pop: int, d: Dims, lanes=None, stream=None):
     _check(_lib.neat_lanes_pack(_ptr(transformed), pop, d, _ptr(lanes), lanes.numel() * lanes.element_size(),
                                 _stream(stream)), "neat_lanes_pack")
     return lanes
+
+
+def neat_lanes_pack_recurrent(transformed, pop: int, d: Dims, lanes=None, stream=None):
+    """Compile recurrent lane programs from records of
+    neat_transform_recurrent; returns the lanes buffer (uint8 CUDA tensor)."""
+    import torch
+    nbytes = neat_lanes_bytes(pop, d)
+    if nbytes == 0:
+        raise NeatError(NEAT_EINVAL, "neat_lanes_bytes (dims not supported by lane programs)")
+    if lanes is None:
+        lanes = torch.empty(nbytes, dtype=torch.uint8, device=transformed.device)
+    _check(_lib.neat_lanes_pack_recurrent(_ptr(transformed), pop, d, _ptr(lanes),
+                                          lanes.numel() * lanes.element_size(), _stream(stream)),
+           "neat_lanes_pack_recurrent")
+    return lanes
+
+
+def neat_forward_lanes_recurrent(lanes, pop: int, d: Dims, inputs, iterations: int, outputs=None,
+                                 stage_bytes: int = 0, pdl: bool = False, stream=None):
+    """`iterations` recurrent iterations from lane programs: inputs f32 [P][I]
+    (or [P][1][I]) -> outputs f32 with the same leading shape and O last."""
+    import torch
+    assert inputs.is_contiguous() and inputs.numel() == pop * d.num_inputs
+    if outputs is None:
+        outputs = torch.empty(tuple(inputs.shape[:-1]) + (d.num_outputs,), dtype=torch.float32, device=inputs.device)
+    _check(_lib.neat_forward_lanes_recurrent(_ptr(lanes), pop, d, _ptr(inputs), iterations, _ptr(outputs),
+                                             stage_bytes, int(pdl), _stream(stream)), "neat_forward_lanes_recurrent")
+    return outputs
 
 
 def neat_lanes_query(lanes) -> LanesInfo:
