@@ -374,7 +374,9 @@ NEAT_API int neat_lanes_pack_recurrent(const void *transformed_dev, int32_t pop,
  * non-input node from iteration k-1's values, the outputs are the values
  * after the last iteration (0 for non-input outputs when iterations is 0).
  * stage_bytes as for neat_forward_lanes (0: the smaller of warp_stride and
- * 48 KB); pdl = 1 launches with programmatic dependent launch (the programs
+ * 48 KB; neat_lanes_info.max_warp_bytes from neat_lanes_query stages every
+ * program with the least shared memory, which is what keeps a population's
+ * blocks in one wave); pdl = 1 launches with programmatic dependent launch (the programs
  * are staged while the previous kernel in the stream drains; the inputs
  * are read after it completes).  NaN outputs for genomes with an error bit
  * and for a buffer packed by neat_lanes_pack.  Errors: NEAT_EINVAL
