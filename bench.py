@@ -880,7 +880,11 @@ def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
     neat_serve_* at several HBM budgets (small ones make admission wait;
     a request that can never fit a budget is refused and counted).  The last
     step's outputs of three requests are checked against the FP64 oracle
-    (16 genomes each, observations regenerated with neat_fill_normal)."""
+    (16 genomes each, observations regenerated with neat_fill_normal).
+    Beside it, the plain form on the same stream: one request at a time in
+    arrival order, each a transform and one neat_forward launch per step
+    (no request shares a launch), latency from the request's scheduled
+    arrival; its outputs equal the served ones bit for bit."""
     import collections
     import concurrent.futures as cf
     import threading
@@ -893,6 +897,7 @@ def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
     reqs = W.serving_requests(0, n_requests)
     results = {}
     parity = None
+    served_last = {}                     # last-step outputs of a few requests, largest budget
     for budget_mb in budgets_mb:
         budget = int(budget_mb) << 20
         srv = neat.Server(budget, max_active=256)
@@ -959,8 +964,12 @@ def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
                 errs.append(oracle_error(y[idx].cpu().numpy(), ref)[2])
             parity = {"max_scaled_error": max(errs),
                       "compared": "last step of 3 requests, 16 genomes each, vs the FP64 oracle"}
+        if budget_mb == budgets_mb[-1]:
+            for i, _ in tickets[:8]:
+                served_last[i] = outs[i][0].clone()
         srv.close()
         outs.clear()
+    plain = measure_serving_plain(reqs, served_last)
     best = results[f"{budgets_mb[-1]}MB"]
     line = {"metric": "serving: genome-forwards/s and request latency p50/p99 ms (Poisson 200 req/s)",
             "value": best["genome_forwards_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
@@ -969,8 +978,61 @@ def measure_serving(args, n_requests=2000, budgets_mb=(64, 256, 1024, 16384)):
                        "genomes": "drawn per request (random_dag_population_vec, the Ant recipe at the request's "
                                   "size)", "budgets_mb": list(budgets_mb)},
             "latency_ms": {"p50": best["latency_p50_ms"], "p99": best["latency_p99_ms"]},
-            "budgets": results, "parity": parity}
+            "budgets": results, "plain": plain, "parity": parity}
     return line
+
+
+def measure_serving_plain(reqs, served_last):
+    """The plain form of the serving workload: the same request stream served
+    one request at a time in arrival order, each a transform and one
+    neat_forward launch per step with the server's observations
+    (neat_fill_normal), no two requests in one launch.  Latency counts from
+    the request's scheduled arrival, so it includes the wait behind earlier
+    requests."""
+    import collections
+    import concurrent.futures as cf
+
+    import torch
+    from paper_2404_01817_gb300 import neat
+    from paper_2404_01817_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    pool = cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1))
+    window = collections.deque()
+    nxt, lat, gf, same = 0, [], 0, True
+    with ClockSampler(0) as clocks:
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            while nxt < len(reqs) and nxt < i + 48:
+                window.append(pool.submit(W.request_population_fast, reqs[nxt]))
+                nxt += 1
+            p = window.popleft().result()
+            dt = r["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            d = neat.dims(p.num_inputs, p.num_outputs, p.max_nodes, p.max_conns)
+            rec, _ = neat.neat_transform(torch.from_numpy(p.nodes).to(dev), torch.from_numpy(p.conns).to(dev), d,
+                                         stream=stream)
+            B = r["batch"]
+            obs = torch.empty(p.pop * B * p.num_inputs, device=dev)
+            y = torch.empty((p.pop, B, p.num_outputs), device=dev)
+            L = neat.neat_default_launch(p.pop, d, B)
+            for st in range(r["steps"]):
+                neat.neat_fill_normal(r["seed"], st, obs, stream=stream)
+                neat.neat_forward(rec, p.pop, d, obs.view(p.pop, B, p.num_inputs), y, launch=L, stream=stream)
+            torch.cuda.synchronize(dev)
+            lat.append((time.perf_counter() - t0 - r["arrival_s"]) * 1e3)
+            gf += p.pop * B * r["steps"]
+            if i in served_last:
+                same = same and bool(torch.equal(y, served_last[i]))
+        wall = time.perf_counter() - t0
+    pool.shutdown()
+    return {"latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+            "genome_forwards_per_s": gf / wall, "requests": len(reqs), "wall_s": wall,
+            "outputs_equal_served": same, "compared_with_served": len(served_last),
+            "form": "one request at a time in arrival order: neat_transform, then one neat_forward launch per "
+                    "step (observations from neat_fill_normal); latency from the scheduled arrival",
+            "clocks": clocks.summary()}
 
 
 def oracle_cores(fn, n_items, chunks_per_core=4):
