@@ -41,6 +41,10 @@ struct CppnArgs {
 
 __device__ unsigned int g_cppn_error;
 
+// QPT: queries per thread evaluated together (1, or 2 in columns tid and
+// tid + 256 of a 512-column tile, sharing each node's entry, dispatch and
+// edge entries); every query's value is bit-equal either way.
+template <int QPT>
 __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
 {
     extern __shared__ __align__(16) uint4 smem[];
@@ -51,7 +55,7 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     const long q0 = (long)(blockIdx.x - (long)g * a.chunks) * (kCppnThreads * kCppnQueriesPerThread);
     uint4 *srec = smem;
     float *v = reinterpret_cast<float *>(smem + a.rec_words);
-    float2 *nodexy = reinterpret_cast<float2 *>(v + (size_t)a.N * kCppnThreads);   // (x, y) of node i
+    float2 *nodexy = reinterpret_cast<float2 *>(v + (size_t)a.N * kCppnThreads * QPT);   // (x, y) of node i
     const uint32_t bar = smem_addr(&bar_mem);
     const uint8_t *grec = a.rec + (size_t)g * a.stride;
     if (tid == 0) {
@@ -90,8 +94,8 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     const uint4 *nodes = srec + 2;
     const uint2 *edges = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(srec) + h1.y);
     const uint16_t *io = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(srec) + h1.w);
-    constexpr int lgT = 8;                              // log2(kCppnThreads): value slot = (p << 8) + tid
-    static_assert((1 << lgT) == kCppnThreads, "tile of the CPPN value array");
+    constexpr int lgT = QPT == 2 ? 9 : 8;               // value slot = (p << lgT) + column
+    static_assert((1 << lgT) == kCppnThreads * QPT, "tile of the CPPN value array");
     const int pin0 = io[0], pin1 = io[1], pin2 = io[2], pin3 = io[3], pin4 = io[4], pout = io[5];
     const int per_block = a.res * a.res * a.res * a.res;
     const int rr = a.res * a.res;
@@ -99,37 +103,68 @@ __global__ void __launch_bounds__(kCppnThreads) cppn_kernel(const CppnArgs a)
     // it by kCppnThreads without dividing
     int r = (int)((q0 + tid) % per_block);
     int s = r / rr, t = r - s * rr;
-    for (long q = q0 + tid; q < qend; q += kCppnThreads) {
+    auto advance = [&](int &r_, int &s_, int &t_) {
+        r_ += kCppnThreads;
+        t_ += kCppnThreads;
+        if (r_ >= per_block) {                         // into the next layer block
+            r_ -= per_block;
+            s_ = r_ / rr;
+            t_ = r_ - s_ * rr;
+        } else {
+            while (t_ >= rr) {
+                t_ -= rr;
+                ++s_;
+            }
+        }
+    };
+    auto put_inputs = [&](int s_, int t_, int col) {
         float2 ps, pt;
         if (a.use_xy) {
-            ps = nodexy[s];
-            pt = nodexy[t];
+            ps = nodexy[s_];
+            pt = nodexy[t_];
         } else {
-            ps = make_float2(coord[s % a.res], coord[s / a.res]);
-            pt = make_float2(coord[t % a.res], coord[t / a.res]);
+            ps = make_float2(coord[s_ % a.res], coord[s_ / a.res]);
+            pt = make_float2(coord[t_ % a.res], coord[t_ / a.res]);
         }
-        v[(pin0 << lgT) + tid] = ps.x;
-        v[(pin1 << lgT) + tid] = ps.y;
-        v[(pin2 << lgT) + tid] = pt.x;
-        v[(pin3 << lgT) + tid] = pt.y;
-        v[(pin4 << lgT) + tid] = 1.0f;
-        if (sum_only)
-            for (int p = first; p < n_nodes; ++p) eval_node_sum_by_count<false>(nodes[p], edges, v, p, lgT, tid);
-        else
-            for (int p = first; p < n_nodes; ++p) eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid);
-        const float w = v[(pout << lgT) + tid];
-        out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
-        r += kCppnThreads;
-        t += kCppnThreads;
-        if (r >= per_block) {                          // into the next layer block
-            r -= per_block;
-            s = r / rr;
-            t = r - s * rr;
-        } else {
-            while (t >= rr) {
-                t -= rr;
-                ++s;
+        v[(pin0 << lgT) + col] = ps.x;
+        v[(pin1 << lgT) + col] = ps.y;
+        v[(pin2 << lgT) + col] = pt.x;
+        v[(pin3 << lgT) + col] = pt.y;
+        v[(pin4 << lgT) + col] = 1.0f;
+    };
+    for (long q = q0 + tid; q < qend; q += (long)kCppnThreads * QPT) {
+        put_inputs(s, t, tid);
+        if (QPT == 2) {
+            int r2 = r, s2 = s, t2 = t;
+            advance(r2, s2, t2);                       // the thread's next query, in column tid + 256
+            put_inputs(s2, t2, tid + kCppnThreads);
+            if (sum_only) {
+                for (int p = first; p < n_nodes; ++p)
+                    eval_node_sum_by_count2(nodes[p], edges, v, p, lgT, tid, kCppnThreads);
+            } else {
+                for (int p = first; p < n_nodes; ++p) {
+                    eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid);
+                    eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid + kCppnThreads);
+                }
             }
+            const float w = v[(pout << lgT) + tid];
+            out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
+            if (q + kCppnThreads < qend) {
+                const float w2 = v[(pout << lgT) + tid + kCppnThreads];
+                out[q + kCppnThreads] = (fabsf(w2) < a.threshold) ? 0.0f : w2;
+            }
+            r = r2;
+            s = s2;
+            t = t2;
+            advance(r, s, t);
+        } else {
+            if (sum_only)
+                for (int p = first; p < n_nodes; ++p) eval_node_sum_by_count<false>(nodes[p], edges, v, p, lgT, tid);
+            else
+                for (int p = first; p < n_nodes; ++p) eval_node_tile<false>(nodes[p], edges, v, p, lgT, tid);
+            const float w = v[(pout << lgT) + tid];
+            out[q] = (fabsf(w) < a.threshold) ? 0.0f : w;
+            advance(r, s, t);
         }
     }
 }
@@ -169,15 +204,20 @@ extern "C" int neat_cppn_query(const void *transformed_dev, int32_t pop, neat_di
     a.threshold = threshold;
     a.rec_words = (int)(record_max_bytes(5, 1, d.max_nodes, d.max_conns) / 16);
     a.use_xy = (r2 <= 4096) ? 1 : 0;
-    const size_t smem = (size_t)a.rec_words * 16 + 4u * (size_t)d.max_nodes * kCppnThreads +
-                        (a.use_xy ? 8u * (size_t)r2 : 0u);
+    // two queries per thread where the doubled value tile fits, else one
+    auto smem_for = [&](int qpt) {
+        return (size_t)a.rec_words * 16 + 4u * (size_t)d.max_nodes * kCppnThreads * qpt +
+               (a.use_xy ? 8u * (size_t)r2 : 0u);
+    };
+    const int qpt = smem_for(2) <= 200u * 1024u ? 2 : 1;
+    const size_t smem = smem_for(qpt);
     if (smem > 200u * 1024u) return invalid("neat_cppn_query: genome too large for one block (max_nodes <= 160)");
     const long blocks = (long)pop * a.chunks;
     if (blocks > 0x7fffffffL) return invalid("neat_cppn_query: too many queries");
-    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(cppn_kernel), smem,
-                                "neat_cppn_query: shared memory per block");
+    auto kern = qpt == 2 ? cppn_kernel<2> : cppn_kernel<1>;
+    int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_cppn_query: shared memory per block");
     if (rc) return rc;
-    cppn_kernel<<<(unsigned)blocks, kCppnThreads, smem, as_stream(stream)>>>(a);
+    kern<<<(unsigned)blocks, kCppnThreads, smem, as_stream(stream)>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_cppn_query: launch");
     return NEAT_OK;

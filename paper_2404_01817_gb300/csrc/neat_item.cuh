@@ -222,6 +222,55 @@ __device__ __forceinline__ void eval_node_sum_by_count(const uint4 ne, const uin
     v[vslot<T1>(p, lgT, col)] = activate(act, fmaf(__uint_as_float(ne.y), a, __uint_as_float(ne.x)));
 }
 
+// The sums of a node's EC edges (EC known at compile time) for two columns
+// col and col + off of the same node row: each column's operations are
+// those of agg_edges_fixed<false, kAggSum, EC> in the same order (the same
+// bits); the edge entries are loaded once for both.
+template <int EC>
+__device__ __forceinline__ float2 sum_edges_fixed2(const uint2 *__restrict__ e, const float *__restrict__ v, int lgT,
+                                                   int col, int off)
+{
+    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < EC; ++i) {
+        const uint2 t = e[i];
+        const int s = vslot<false>(t.y, lgT, col);
+        a[i & 3] = fmaf(__uint_as_float(t.x), v[s], a[i & 3]);
+        b[i & 3] = fmaf(__uint_as_float(t.x), v[s + off], b[i & 3]);
+    }
+    return make_float2((a[0] + a[1]) + (a[2] + a[3]), (b[0] + b[1]) + (b[2] + b[3]));
+}
+
+// Two columns of eval_node_sum_by_count: the node entry, the dispatch on the
+// edge count and the edge entries shared; each column's value bit-equal to
+// a one-column evaluation.  For callers whose warp is on one node.
+__device__ __forceinline__ void eval_node_sum_by_count2(const uint4 ne, const uint2 *__restrict__ edges,
+                                                        float *__restrict__ v, int p, int lgT, int col, int off)
+{
+    const uint32_t act = ne.w & 0xffu;
+    if (act == kInputAct) return;
+    const uint32_t ec = ne.z >> 16;
+    const uint2 *e = edges + (ne.z & 0xffffu);
+    float2 a;
+    switch (ec) {
+    case 0: a = sum_edges_fixed2<0>(e, v, lgT, col, off); break;
+    case 1: a = sum_edges_fixed2<1>(e, v, lgT, col, off); break;
+    case 2: a = sum_edges_fixed2<2>(e, v, lgT, col, off); break;
+    case 3: a = sum_edges_fixed2<3>(e, v, lgT, col, off); break;
+    case 4: a = sum_edges_fixed2<4>(e, v, lgT, col, off); break;
+    case 5: a = sum_edges_fixed2<5>(e, v, lgT, col, off); break;
+    case 6: a = sum_edges_fixed2<6>(e, v, lgT, col, off); break;
+    case 7: a = sum_edges_fixed2<7>(e, v, lgT, col, off); break;
+    case 8: a = sum_edges_fixed2<8>(e, v, lgT, col, off); break;
+    default:
+        a = make_float2(partials<false, true>(kAggSum, e, ec, v, lgT, col, 0, 4),
+                        partials<false, true>(kAggSum, e, ec, v, lgT, col + off, 0, 4));
+    }
+    const int s = vslot<false>((uint32_t)p, lgT, col);
+    v[s] = activate(act, fmaf(__uint_as_float(ne.y), a.x, __uint_as_float(ne.x)));
+    v[s + off] = activate(act, fmaf(__uint_as_float(ne.y), a.y, __uint_as_float(ne.x)));
+}
+
 // One whole node for one column when every non-input node of the genome
 // aggregates by sum (any activation): no aggregation dispatch.
 template <bool T1>
