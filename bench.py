@@ -672,8 +672,8 @@ def run_distance(args, R=64):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": src,
                          "note": "distance kernel; algorithmic bytes = used gene-record bytes of both sides + the "
-                                 "f32 distance matrix; the kernel is bound by instruction issue (hash lookups "
-                                 "in shared memory and warp reductions), not by HBM"},
+                                 "f32 distance matrix; the kernel is bound by instruction issue (one union-table "
+                                 "probe per gene, per-representative row reads and warp reductions), not by HBM"},
             "cpu_baseline": {"value": idx.size * R / dt_all, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": f"{idx.size} genomes x {R} representatives, FP64 C oracle (all-pairs "
                                        f"gene matching), {cores} threads",

@@ -16,10 +16,14 @@
 //    gene record: header, sorted node keys, node attributes, sorted pair
 //    keys, connection attributes.  Duplicates show up as equal neighbours.
 //  * neat_distance: a block stages a tile of up to 16 b-records in shared
-//    memory with TMA bulk copies (one mbarrier, bounded wait) and builds an
-//    open-addressing hash table of each record's node keys and connection
-//    pairs next to it (records too large for tables are searched by binary
-//    search in their sorted keys instead).  Its warps stream a-genomes from
+//    memory with TMA bulk copies (one mbarrier, bounded wait) and indexes
+//    them in one of three ways: for small genomes (at most 255 node and 255
+//    connection genes) one open-addressing table per gene kind over the
+//    union of the tile's keys, each entry holding the key's row index in
+//    every staged record (one byte per record, 0xFF where absent), so a gene
+//    is probed once for the whole tile; otherwise one hash table per record;
+//    records too large for tables are searched by binary search in their
+//    sorted keys.  Its warps stream a-genomes from
 //    global memory (L2-resident across blocks): lane l loads a's genes l,
 //    l+32, ... once each and looks every one up in all staged b-records
 //    (independent lookups in flight, per-representative sums in registers);
@@ -178,9 +182,15 @@ struct DistArgs {
     long long ldo;
     int tile;             // b-records per block
     int a_per_block;      // a-genomes per block
-    uint32_t slot_bytes;  // shared memory per staged b-record: the record, then (HASH) its two tables
-    uint32_t lgn, lgc;    // log2 of the node / connection hash-table capacities (HASH)
+    uint32_t slot_bytes;  // shared memory per staged b-record: the record, then (kHash) its two tables
+    uint32_t lgn, lgc;    // log2 of the node / connection hash-table capacities (kHash, kUnion)
+    uint32_t union_off;   // offset of the two union tables after the staged records (kUnion)
 };
+
+// How a block finds a-genes in its staged b-records.
+constexpr int kSearch = 0;   // binary search in each record's sorted keys
+constexpr int kHash = 1;     // one hash table per record
+constexpr int kUnion = 2;    // one table over the tile's keys, row indices of every record per entry
 
 __device__ unsigned int g_distance_error;
 
@@ -246,6 +256,95 @@ __device__ __forceinline__ int conn_lookup(const unsigned long long *tab, uint32
     return -1;
 }
 
+// Union tables (kUnion) of 16-byte entries: node entries {key, row indices
+// in records 0-3, in records 4-7, unused}, connection entries {pair (64
+// bits), row indices in records 0-3, in records 4-7}, one index byte per
+// staged record.  Every byte starts at 0xFF: a free entry has key 0xFFFFFFFF
+// (keys are below 2^24) or pair ~0 (pairs have 48 bits), and index 0xFF
+// means the record lacks the gene.  Linear probing; capacities are powers of
+// two above 1.25x the largest union a tile can have, so a probe sequence
+// always reaches a free entry.  Rows of one record are distinct per key
+// (duplicates make an error record, which holds no genes), so each index
+// byte has one writer.
+constexpr int kUnionMaxTile = 8;
+
+__device__ __forceinline__ void union_insert_node(uint4 *tab, uint32_t lg, uint32_t key, int t, uint32_t row)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(key, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t old = atomicCAS(&tab[s].x, 0xffffffffu, key);
+        if (old == 0xffffffffu || old == key) {
+            reinterpret_cast<unsigned char *>(tab + s)[4 + t] = (unsigned char)row;
+            return;
+        }
+        s = (s + 1u) & mask;
+    }
+}
+
+__device__ __forceinline__ void union_insert_conn(uint4 *tab, uint32_t lg, unsigned long long pair, int t,
+                                                  uint32_t row)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(fold_pair(pair), lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long *>(tab + s), kEmpty, pair);
+        if (old == kEmpty || old == pair) {
+            reinterpret_cast<unsigned char *>(tab + s)[8 + t] = (unsigned char)row;
+            return;
+        }
+        s = (s + 1u) & mask;
+    }
+}
+
+// The index bytes of `key` (records 0-3, records 4-7); all 0xFF when no
+// staged record has it.
+__device__ __forceinline__ uint2 union_find_node(const uint4 *tab, uint32_t lg, uint32_t key)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(key, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint4 e = tab[s];
+        if (e.x == key) return make_uint2(e.y, e.z);
+        if (e.x == 0xffffffffu) break;
+        s = (s + 1u) & mask;
+    }
+    return make_uint2(~0u, ~0u);
+}
+
+__device__ __forceinline__ uint2 union_find_conn(const uint4 *tab, uint32_t lg, unsigned long long pair)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = slot_of(fold_pair(pair), lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint4 e = tab[s];
+        if ((((unsigned long long)e.y << 32) | e.x) == pair) return make_uint2(e.z, e.w);
+        if (e.y == 0xffffffffu) break;
+        s = (s + 1u) & mask;
+    }
+    return make_uint2(~0u, ~0u);
+}
+
+// Row of record t among the index bytes of a union entry (t a constant
+// after unrolling).
+__device__ __forceinline__ uint32_t union_row(uint2 ix, int t)
+{
+    return ((t < 4 ? ix.x : ix.y) >> (8 * (t & 3))) & 0xffu;
+}
+
+// One homologous gene pair's distance terms.
+__device__ __forceinline__ float node_term(uint4 x, uint4 y)
+{
+    return fabsf(__uint_as_float(x.x) - __uint_as_float(y.x)) + fabsf(__uint_as_float(x.y) - __uint_as_float(y.y)) +
+           ((__uint_as_float(x.z) != __uint_as_float(y.z)) ? 1.0f : 0.0f) +
+           ((__uint_as_float(x.w) != __uint_as_float(y.w)) ? 1.0f : 0.0f);
+}
+
+__device__ __forceinline__ float conn_term(float2 x, float2 y)
+{
+    return fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -253,9 +352,10 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-template <bool HASH, int TILE>
+template <int MODE, int TILE>
 __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p)
 {
+    static_assert(MODE != kUnion || TILE <= kUnionMaxTile, "union entries hold 8 index bytes");
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar_mem;
     __shared__ int failed;
@@ -279,13 +379,19 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
             bulk_g2s(smem_addr(sm + (size_t)t * p.slot_bytes), src, bytes, bar);
         }
     }
-    if constexpr (HASH) {
+    if constexpr (MODE == kHash) {
         // the tables sit after each record's stride, outside the copied bytes
         const uint32_t words = (p.slot_bytes - (uint32_t)p.stride) / 8u;
         for (int t = 0; t < nb; ++t) {
             unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm + (size_t)t * p.slot_bytes + p.stride);
             for (uint32_t i = tid; i < words; i += kDistThreads) tab[i] = kEmpty;
         }
+    }
+    if constexpr (MODE == kUnion) {
+        // after the tile's records, outside the copied bytes
+        uint4 *u = reinterpret_cast<uint4 *>(sm + p.union_off);
+        const uint32_t entries = (1u << p.lgn) + (1u << p.lgc);
+        for (uint32_t i = tid; i < entries; i += kDistThreads) u[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
     }
     __syncthreads();
     if (!mbar_wait(bar, 0)) failed = 1;
@@ -309,7 +415,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         s_ckey[tid] = Lb.ckey;
         s_cattr[tid] = Lb.cattr;
     }
-    if constexpr (HASH) {
+    if constexpr (MODE == kHash) {
         for (int t = 0; t < nb; ++t) {
             unsigned char *rb = sm + (size_t)t * p.slot_bytes;
             const uint4 hb = *reinterpret_cast<const uint4 *>(rb);
@@ -322,6 +428,21 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                 table_insert(ntab, p.lgn, slot_of(nkey[j], p.lgn), ((unsigned long long)nkey[j] << 32) | j);
             for (uint32_t j = tid; j < hb.y; j += kDistThreads)
                 table_insert(ctab, p.lgc, slot_of(fold_pair(ckey[j]), p.lgc), (ckey[j] << 13) | j);
+        }
+    }
+    if constexpr (MODE == kUnion) {
+        uint4 *un = reinterpret_cast<uint4 *>(sm + p.union_off);
+        uint4 *uc = un + (1u << p.lgn);
+        for (int t = 0; t < nb; ++t) {
+            const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+            const uint4 hb = *reinterpret_cast<const uint4 *>(rb);
+            const GeneLayout Lb = gene_layout(hb.x, hb.y);
+            const uint32_t *nkey = reinterpret_cast<const uint32_t *>(rb + Lb.nkey);
+            const unsigned long long *ckey = reinterpret_cast<const unsigned long long *>(rb + Lb.ckey);
+            // an index byte addresses rows 0-254 (the host takes this form
+            // only for at most 255 genes of each kind)
+            for (uint32_t j = tid; j < min(hb.x, 255u); j += kDistThreads) union_insert_node(un, p.lgn, nkey[j], t, j);
+            for (uint32_t j = tid; j < min(hb.y, 255u); j += kDistThreads) union_insert_conn(uc, p.lgc, ckey[j], t, j);
         }
     }
     __syncthreads();
@@ -348,22 +469,35 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
             for (int j = lane; j < n_a; j += 32) {
                 const uint32_t key = __ldg(ka + j);
                 const uint4 x = __ldg(aa + j);
+                if constexpr (MODE == kUnion) {
+                    // one probe for the tile, then the rows it names
+                    const uint2 ix = union_find_node(reinterpret_cast<const uint4 *>(sm + p.union_off), p.lgn, key);
 #pragma unroll
-                for (int t = 0; t < TILE; ++t) {
-                    if (t < nb) {
-                        const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
-                        int i;
-                        if constexpr (HASH)
-                            i = node_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride), p.lgn, key);
-                        else
-                            i = find_key(reinterpret_cast<const uint32_t *>(rb + kGeneHeaderBytes), (int)s_n[t], key);
-                        if (i >= 0) {
-                            const uint4 y = reinterpret_cast<const uint4 *>(rb + s_nattr[t])[i];
+                    for (int t = 0; t < TILE; ++t) {
+                        const uint32_t i = union_row(ix, t);
+                        if (i != 0xffu) {
+                            const uint4 y = reinterpret_cast<const uint4 *>(sm + (size_t)t * p.slot_bytes + s_nattr[t])[i];
                             ++hn[t];
-                            sn[t] += fabsf(__uint_as_float(x.x) - __uint_as_float(y.x)) +
-                                     fabsf(__uint_as_float(x.y) - __uint_as_float(y.y)) +
-                                     ((__uint_as_float(x.z) != __uint_as_float(y.z)) ? 1.0f : 0.0f) +
-                                     ((__uint_as_float(x.w) != __uint_as_float(y.w)) ? 1.0f : 0.0f);
+                            sn[t] += node_term(x, y);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < TILE; ++t) {
+                        if (t < nb) {
+                            const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+                            int i;
+                            if constexpr (MODE == kHash)
+                                i = node_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride), p.lgn,
+                                                key);
+                            else
+                                i = find_key(reinterpret_cast<const uint32_t *>(rb + kGeneHeaderBytes), (int)s_n[t],
+                                             key);
+                            if (i >= 0) {
+                                const uint4 y = reinterpret_cast<const uint4 *>(rb + s_nattr[t])[i];
+                                ++hn[t];
+                                sn[t] += node_term(x, y);
+                            }
                         }
                     }
                 }
@@ -394,20 +528,36 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
             for (int j = lane; j < m_a; j += 32) {
                 const unsigned long long key = __ldg(ka + j);
                 const float2 x = __ldg(aa + j);
+                if constexpr (MODE == kUnion) {
+                    const uint2 ix = union_find_conn(reinterpret_cast<const uint4 *>(sm + p.union_off) + (1u << p.lgn),
+                                                     p.lgc, key);
 #pragma unroll
-                for (int t = 0; t < TILE; ++t) {
-                    if (t < nb) {
-                        const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
-                        int i;
-                        if constexpr (HASH)
-                            i = conn_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride) + (1u << p.lgn),
-                                            p.lgc, key);
-                        else
-                            i = find_key(reinterpret_cast<const unsigned long long *>(rb + s_ckey[t]), (int)s_m[t], key);
-                        if (i >= 0) {
-                            const float2 y = reinterpret_cast<const float2 *>(rb + s_cattr[t])[i];
+                    for (int t = 0; t < TILE; ++t) {
+                        const uint32_t i = union_row(ix, t);
+                        if (i != 0xffu) {
+                            const float2 y = reinterpret_cast<const float2 *>(sm + (size_t)t * p.slot_bytes + s_cattr[t])[i];
                             ++hc[t];
-                            sc[t] += fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
+                            sc[t] += conn_term(x, y);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < TILE; ++t) {
+                        if (t < nb) {
+                            const unsigned char *rb = sm + (size_t)t * p.slot_bytes;
+                            int i;
+                            if constexpr (MODE == kHash)
+                                i = conn_lookup(reinterpret_cast<const unsigned long long *>(rb + p.stride) +
+                                                    (1u << p.lgn),
+                                                p.lgc, key);
+                            else
+                                i = find_key(reinterpret_cast<const unsigned long long *>(rb + s_ckey[t]), (int)s_m[t],
+                                             key);
+                            if (i >= 0) {
+                                const float2 y = reinterpret_cast<const float2 *>(rb + s_cattr[t])[i];
+                                ++hc[t];
+                                sc[t] += conn_term(x, y);
+                            }
                         }
                     }
                 }
@@ -569,9 +719,38 @@ extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *gen
     p.slot_bytes = (uint32_t)(hash ? slot_hash : p.stride);
     const size_t per_block = p.slot_bytes <= shared_budget ? shared_budget : budget;
     p.tile = (int)std::min<size_t>({(size_t)kMaxTile, per_block / p.slot_bytes, (size_t)pop_b});
+    p.union_off = 0;
+    size_t smem = (size_t)p.tile * p.slot_bytes;
+    // union tables (at most 255 genes of each kind: byte row indices) of
+    // capacity 2^lg > 1.25x the tile's largest possible union, taken when
+    // they stage as many records per block as the per-record tables (up to
+    // 8, the records an entry indexes), three blocks per SM: a gene is then
+    // probed once per tile instead of once per record
+    bool use_union = false;
+    if (d.max_nodes <= 255 && d.max_conns <= 255) {
+        auto lg_union = [](long n) {
+            uint32_t lg = 1;
+            while ((1L << lg) < n + n / 4 + 1) ++lg;
+            return lg;
+        };
+        const int want = std::min(kUnionMaxTile, p.tile);
+        for (int t = std::min(kUnionMaxTile, (int)pop_b); t >= want; --t) {
+            const uint32_t ln = lg_union((long)t * d.max_nodes), lc = lg_union((long)t * d.max_conns);
+            const size_t bytes = (size_t)t * p.stride + 16u * ((size_t(1) << ln) + (size_t(1) << lc));
+            if (bytes <= shared_budget) {
+                use_union = true;
+                p.tile = t;
+                p.lgn = ln;
+                p.lgc = lc;
+                p.slot_bytes = (uint32_t)p.stride;
+                p.union_off = (uint32_t)((size_t)t * p.stride);
+                smem = bytes;
+                break;
+            }
+        }
+    }
     const int tiles = (pop_b + p.tile - 1) / p.tile;
     if (tiles > 65535) return invalid("neat_distance: too many b-genomes");
-    const size_t smem = (size_t)p.tile * p.slot_bytes;
     int dev = 0, sms = 152, smem_sm = 228 * 1024;
     if (cudaGetDevice(&dev) == cudaSuccess) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -586,11 +765,22 @@ extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *gen
     const long gx = (pop_a + p.a_per_block - 1) / p.a_per_block;
     using Kern = void (*)(DistArgs);
     Kern kern;
-    if (p.tile > 8) kern = hash ? distance_kernel<true, 16> : distance_kernel<false, 16>;
-    else if (p.tile > 4) kern = hash ? distance_kernel<true, 8> : distance_kernel<false, 8>;
-    else if (p.tile > 2) kern = hash ? distance_kernel<true, 4> : distance_kernel<false, 4>;
-    else if (p.tile > 1) kern = hash ? distance_kernel<true, 2> : distance_kernel<false, 2>;
-    else kern = hash ? distance_kernel<true, 1> : distance_kernel<false, 1>;
+    if (use_union) {
+        if (p.tile > 4) kern = distance_kernel<kUnion, 8>;
+        else if (p.tile > 2) kern = distance_kernel<kUnion, 4>;
+        else if (p.tile > 1) kern = distance_kernel<kUnion, 2>;
+        else kern = distance_kernel<kUnion, 1>;
+    } else if (p.tile > 8) {
+        kern = hash ? distance_kernel<kHash, 16> : distance_kernel<kSearch, 16>;
+    } else if (p.tile > 4) {
+        kern = hash ? distance_kernel<kHash, 8> : distance_kernel<kSearch, 8>;
+    } else if (p.tile > 2) {
+        kern = hash ? distance_kernel<kHash, 4> : distance_kernel<kSearch, 4>;
+    } else if (p.tile > 1) {
+        kern = hash ? distance_kernel<kHash, 2> : distance_kernel<kSearch, 2>;
+    } else {
+        kern = hash ? distance_kernel<kHash, 1> : distance_kernel<kSearch, 1>;
+    }
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(kern), smem, "neat_distance: shared memory per block");
     if (rc) return rc;
     kern<<<dim3((unsigned)gx, (unsigned)tiles), kDistThreads, smem, as_stream(stream)>>>(p);

@@ -123,6 +123,37 @@ def test_tiling_does_not_change_bits(neat):
     np.testing.assert_array_equal(part, full[7:297, 5:14])
 
 
+def _pad(a, rows):
+    out = np.full((a.shape[0], rows, a.shape[2]), np.nan, np.float32)
+    out[:, :a.shape[1]] = a
+    return out
+
+
+def test_table_forms_agree_bit_for_bit(neat):
+    """The same genomes through the three ways a block indexes its staged
+    records, chosen by the dims alone: union tables over the tile's keys (at
+    most 255 genes of each kind), one hash table per record (300 nodes) and
+    binary search (1024 nodes / 8192 connections).  Records are compact, so
+    the distances must agree bit for bit; 21 representatives leave a partial
+    last tile, and two error genomes give NaN rows and columns."""
+    p = _related(11, 130)
+    nodes, conns = p.nodes.copy(), p.conns.copy()
+    rn = np.flatnonzero(~np.isnan(nodes[4, :, 0]))
+    nodes[4, rn[1]] = nodes[4, rn[0]]                        # a duplicated node key
+    rc = np.flatnonzero(~np.isnan(conns[17, :, 0]))
+    conns[17, rc[1]] = conns[17, rc[0]]                      # a duplicated connection pair
+    ref, _, _ = oracle.distance(nodes, conns, nodes[:21], conns[:21], 1.0, 0.5)
+    outs = []
+    for nmax, cmax in ((24, 60), (300, 400), (1024, 8192)):
+        d, genes, st = _prepare(neat, _pad(nodes, nmax), _pad(conns, cmax))
+        assert st[4] and st[17] and np.count_nonzero(st) == 2
+        outs.append(neat.neat_distance(genes, 130, genes, 21, d, 1.0, 0.5).cpu().numpy())
+    assert_outputs_close(outs[0], ref, what="union tables")
+    assert np.isnan(outs[0][4]).all() and np.isnan(outs[0][:, 17]).all()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
 def test_invalid_and_empty_genomes(neat):
     ok = genome([(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1)], [(0, 1, 1, 0.5), None], 3, 2)
     dupkey = genome([(0, 0, 1, 0, 0), (1, 0.2, 1, 0, 1), (1, 0.3, 1, 0, 1)], [(0, 1, 1, 0.5), None], 3, 2)
