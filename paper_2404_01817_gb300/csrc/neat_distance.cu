@@ -11,10 +11,14 @@
 // node and connection gene counts, and a term with a zero denominator 0.
 //
 // GB300 mapping:
-//  * neat_distance_prepare: one block per genome sorts its node keys and its
-//    connection key pairs in shared memory (bitonic) and writes a compact
-//    gene record: header, sorted node keys, node attributes, sorted pair
-//    keys, connection attributes.  Duplicates show up as equal neighbours.
+//  * neat_distance_prepare: each genome's node keys and connection key pairs
+//    are sorted (bitonic) and written as a compact gene record: header,
+//    sorted node keys, node attributes, sorted pair keys, connection
+//    attributes.  Duplicates show up as equal neighbours.  Genomes of at most
+//    64 node rows and 256 connection rows take one warp each: present rows
+//    are compacted by ballots, and the keys, padded to the next power of
+//    two, are sorted in registers across the warp's lanes by shuffles;
+//    larger genomes take one block each and sort in shared memory.
 //  * neat_distance: a block stages a tile of up to 16 b-records in shared
 //    memory with TMA bulk copies (one mbarrier, bounded wait) and indexes
 //    them in one of three ways: for small genomes (at most 255 node and 255
@@ -76,7 +80,11 @@ struct PrepArgs {
     uint32_t *status;
     size_t stride;
     int N, C, Np2, Cp2;
+    int pop;
 };
+
+constexpr int kPrepWarpGenomes = 4;   // genomes (one per warp) per block of the warp form
+constexpr int kWarpMaxNodes = 64, kWarpMaxConns = 256;
 
 __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
 {
@@ -167,6 +175,187 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
         ocattr[j] = make_float2(row.w, row.z != 0.0f ? 1.0f : 0.0f);
     }
     if (tid == 0) {
+        *reinterpret_cast<uint4 *>(rec) = make_uint4((uint32_t)n, (uint32_t)m, 0u, L.used);
+        if (a.status) a.status[g] = 0u;
+    }
+}
+
+// Ascending bitonic sort of the 32 R keys a warp holds, key e in lane e % 32,
+// register e / 32 (registers R.. of v are left alone).  A compare-exchange
+// partner 32 j' or more positions away sits in another register of the same
+// lane; a nearer one in another lane at the same register.
+template <int R, int NR>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[NR], int lane)
+{
+    static_assert(R <= NR, "registers");
+    constexpr int n2 = 32 * R;
+    for (int k = 2; k <= n2; k <<= 1) {
+#pragma unroll
+        for (int jr = R / 2; jr >= 1; jr >>= 1) {
+            if (32 * jr <= (k >> 1)) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!(r & jr)) {
+                        const bool up = (((r << 5) | lane) & k) == 0;
+                        const unsigned long long x = v[r], y = v[r | jr];
+                        if ((x > y) == up) {
+                            v[r] = y;
+                            v[r | jr] = x;
+                        }
+                    }
+                }
+            }
+        }
+        for (int j = min(k >> 1, 16); j >= 1; j >>= 1) {
+            const bool lower = (lane & j) == 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const unsigned long long x = v[r];
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+                const bool up = (((r << 5) | lane) & k) == 0;
+                // in an ascending run the lower position keeps the smaller key
+                v[r] = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+            }
+        }
+    }
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_bitonic_any(unsigned long long (&v)[NR], int regs, int lane)
+{
+    if (regs <= 1) warp_bitonic<1>(v, lane);
+    else if (regs <= 2) warp_bitonic<(NR < 2 ? NR : 2)>(v, lane);
+    else if (regs <= 4) warp_bitonic<(NR < 4 ? NR : 4)>(v, lane);
+    else warp_bitonic<NR>(v, lane);
+}
+
+// True in some lane when two of the first `count` sorted keys agree in the
+// bits above `shift`.
+template <int NR>
+__device__ __forceinline__ bool warp_has_equal_neighbours(const unsigned long long (&v)[NR], int regs, int count,
+                                                          int shift, int lane)
+{
+    bool dup = false;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        if (r < regs) {
+            const unsigned long long up1 = __shfl_up_sync(0xffffffffu, v[r], 1);
+            const unsigned long long last = r ? __shfl_sync(0xffffffffu, v[r ? r - 1 : 0], 31) : 0ull;
+            const unsigned long long prev = lane ? up1 : last;
+            const int e = (r << 5) | lane;
+            if (e >= 1 && e < count && (v[r] >> shift) == (prev >> shift)) dup = true;
+        }
+    }
+    return dup;
+}
+
+// Gene records, one warp per genome of at most 64 node rows and 256
+// connection rows; the records are those of prepare_kernel.
+__global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(const PrepArgs a)
+{
+    __shared__ unsigned long long s_keys[kPrepWarpGenomes][kWarpMaxNodes + kWarpMaxConns];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kPrepWarpGenomes + warp;
+    if (g >= a.pop) return;
+    unsigned long long *nk = s_keys[warp], *ck = nk + kWarpMaxNodes;
+    const float *nd = a.nodes + (size_t)g * a.N * 5;
+    const float4 *cn = reinterpret_cast<const float4 *>(a.conns + (size_t)g * a.C * 4);
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t st = 0;
+    // present rows, compacted in row order (the sort makes the order moot)
+    int n = 0, m = 0;
+    for (int base = 0; base < a.N; base += 32) {
+        const int r = base + lane;
+        bool ok = false;
+        unsigned long long v = 0;
+        if (r < a.N) {
+            const float k = __ldg(nd + (size_t)r * 5);
+            if (!isnan(k)) {
+                if (is_key(k)) {
+                    ok = true;
+                    v = ((unsigned long long)(uint32_t)k << 32) | (unsigned)r;
+                } else {
+                    st |= NEAT_G_BADKEY;
+                }
+            }
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, ok);
+        if (ok) nk[n + __popc(b & below)] = v;
+        n += __popc(b);
+    }
+    for (int base = 0; base < a.C; base += 32) {
+        const int c = base + lane;
+        bool ok = false;
+        unsigned long long v = 0;
+        if (c < a.C) {
+            const float4 row = __ldg(cn + c);
+            if (!(isnan(row.x) || isnan(row.y) || isnan(row.z))) {
+                if (is_key(row.x) && is_key(row.y)) {
+                    ok = true;
+                    const unsigned long long pair = ((unsigned long long)(uint32_t)row.x << 24) | (uint32_t)row.y;
+                    v = (pair << 13) | (unsigned)c;
+                } else {
+                    st |= NEAT_G_BADKEY;
+                }
+            }
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, ok);
+        if (ok) ck[m + __popc(b & below)] = v;
+        m += __popc(b);
+    }
+    __syncwarp();
+    // n <= 64 and m <= 256 present rows: 2 and 8 registers a lane at most
+    unsigned long long vn[2], vc[8];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int e = (r << 5) | lane;
+        vn[r] = e < n ? nk[e] : ~0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int e = (r << 5) | lane;
+        vc[r] = e < m ? ck[e] : ~0ull;
+    }
+    const int rn = (n + 31) >> 5, rc = (m + 31) >> 5;   // registers in use (0 for none)
+    warp_bitonic_any(vn, rn, lane);
+    warp_bitonic_any(vc, rc, lane);
+    if (warp_has_equal_neighbours(vn, rn, n, 32, lane)) st |= NEAT_G_DUPKEY;
+    if (warp_has_equal_neighbours(vc, rc, m, 13, lane)) st |= NEAT_G_DUPCONN;
+    st = __reduce_or_sync(0xffffffffu, st);
+    uint8_t *rec = a.out + (size_t)g * a.stride;
+    if (st) {
+        if (lane == 0) {
+            *reinterpret_cast<uint4 *>(rec) = make_uint4(0u, 0u, st, kGeneHeaderBytes);
+            if (a.status) a.status[g] = st;
+        }
+        return;
+    }
+    const GeneLayout L = gene_layout((uint32_t)n, (uint32_t)m);
+    uint32_t *okey = reinterpret_cast<uint32_t *>(rec + L.nkey);
+    uint4 *oattr = reinterpret_cast<uint4 *>(rec + L.nattr);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int e = (r << 5) | lane;
+        if (e < n) {
+            const float *row = nd + (size_t)(vn[r] & 0xffffffffu) * 5;
+            okey[e] = (uint32_t)(vn[r] >> 32);
+            oattr[e] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
+                                  __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
+        }
+    }
+    for (int j = n + lane; j < (int)((L.nattr - L.nkey) / 4); j += 32) okey[j] = 0xffffffffu;   // pad
+    unsigned long long *ockey = reinterpret_cast<unsigned long long *>(rec + L.ckey);
+    float2 *ocattr = reinterpret_cast<float2 *>(rec + L.cattr);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int e = (r << 5) | lane;
+        if (e < m) {
+            const float4 row = __ldg(cn + (vc[r] & 0x1fffu));
+            ockey[e] = vc[r] >> 13;
+            ocattr[e] = make_float2(row.w, row.z != 0.0f ? 1.0f : 0.0f);
+        }
+    }
+    if (lane == 0) {
         *reinterpret_cast<uint4 *>(rec) = make_uint4((uint32_t)n, (uint32_t)m, 0u, L.used);
         if (a.status) a.status[g] = 0u;
     }
@@ -345,11 +534,36 @@ __device__ __forceinline__ float conn_term(float2 x, float2 y)
     return fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
 }
 
-__device__ __forceinline__ float warp_sum(float v)
+__host__ __device__ constexpr int log2_tile(int t) { return t >= 16 ? 4 : t >= 8 ? 3 : t >= 4 ? 2 : t >= 2 ? 1 : 0; }
+
+// Warp totals of TILE per-lane values, one reduce-scatter: lane l ends with
+// the total of v[l >> (5 - log2 TILE)].  The first log2 TILE exchange steps
+// (offsets 16, 8, ...) each send half of the lane's remaining values to the
+// partner and keep the other half, the rest add whole values; lanes are
+// paired in the order 16, 8, 4, 2, 1 throughout, so every total is the sum
+// tree of a butterfly reduction of that value alone.
+template <int TILE>
+__device__ __forceinline__ float warp_sum_scatter(const float (&v)[TILE], int lane)
 {
+    constexpr int LG = log2_tile(TILE);
+    static_assert((1 << LG) == TILE, "TILE is a power of two");
+    float w[TILE];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < TILE; ++i) w[i] = v[i];
+#pragma unroll
+    for (int s = 0; s < LG; ++s) {
+        const int o = 16 >> s, half = TILE >> (s + 1);
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = hi ? w[i] : w[i + half];
+            const float keep = hi ? w[i + half] : w[i];
+            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> LG; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    return w[0];
 }
 
 template <int MODE, int TILE>
@@ -446,12 +660,23 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         }
     }
     __syncthreads();
+    // byte offsets of every staged record's node and connection attributes
+    // (0 past the tile: the union form reads a row of every record, and
+    // discards the rows of records that lack the gene)
+    uint32_t noff[TILE], coff[TILE];
+#pragma unroll
+    for (int t = 0; t < TILE; ++t) {
+        noff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_nattr[t] : 0u;
+        coff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_cattr[t] : 0u;
+    }
+    constexpr int LG = log2_tile(TILE);
+    const int out_t = lane >> (5 - LG);              // the representative whose totals this lane ends with
     for (int a = a_begin + warp; a < a_end; a += kDistWarps) {
         const uint8_t *ra = p.a + (size_t)a * p.stride;
         const uint4 ha = __ldg(reinterpret_cast<const uint4 *>(ra));
         const int n_a = (int)ha.x, m_a = (int)ha.y;
         const GeneLayout La = gene_layout(ha.x, ha.y);
-        // lane t ends up with the totals of representative t
+        // lane l ends up with the totals of representative out_t = l >> (5 - log2 TILE)
         int my_hn = 0, my_hc = 0;
         float my_sn = 0.0f, my_sc = 0.0f;
         {
@@ -474,12 +699,12 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                     const uint2 ix = union_find_node(reinterpret_cast<const uint4 *>(sm + p.union_off), p.lgn, key);
 #pragma unroll
                     for (int t = 0; t < TILE; ++t) {
+                        // partial sums are >= +0, so adding +0 for an absent gene changes no bit
                         const uint32_t i = union_row(ix, t);
-                        if (i != 0xffu) {
-                            const uint4 y = reinterpret_cast<const uint4 *>(sm + (size_t)t * p.slot_bytes + s_nattr[t])[i];
-                            ++hn[t];
-                            sn[t] += node_term(x, y);
-                        }
+                        const bool h = i != 0xffu;
+                        const uint4 y = *reinterpret_cast<const uint4 *>(sm + noff[t] + (h ? i : 0u) * 16u);
+                        hn[t] += h;
+                        sn[t] += h ? node_term(x, y) : 0.0f;
                     }
                 } else {
 #pragma unroll
@@ -504,15 +729,10 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
             }
 #pragma unroll
             for (int t = 0; t < TILE; ++t) {
-                if (t < nb) {
-                    const int h = __reduce_add_sync(0xffffffffu, hn[t]);
-                    const float v = warp_sum(sn[t]);
-                    if (lane == t) {
-                        my_hn = h;
-                        my_sn = v;
-                    }
-                }
+                const int h = __reduce_add_sync(0xffffffffu, hn[t]);
+                if (out_t == t) my_hn = h;
             }
+            my_sn = warp_sum_scatter<TILE>(sn, lane);
         }
         {
             // connection genes, the same way
@@ -534,11 +754,10 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
 #pragma unroll
                     for (int t = 0; t < TILE; ++t) {
                         const uint32_t i = union_row(ix, t);
-                        if (i != 0xffu) {
-                            const float2 y = reinterpret_cast<const float2 *>(sm + (size_t)t * p.slot_bytes + s_cattr[t])[i];
-                            ++hc[t];
-                            sc[t] += conn_term(x, y);
-                        }
+                        const bool h = i != 0xffu;
+                        const float2 y = *reinterpret_cast<const float2 *>(sm + coff[t] + (h ? i : 0u) * 8u);
+                        hc[t] += h;
+                        sc[t] += h ? conn_term(x, y) : 0.0f;
                     }
                 } else {
 #pragma unroll
@@ -564,28 +783,23 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
             }
 #pragma unroll
             for (int t = 0; t < TILE; ++t) {
-                if (t < nb) {
-                    const int h = __reduce_add_sync(0xffffffffu, hc[t]);
-                    const float v = warp_sum(sc[t]);
-                    if (lane == t) {
-                        my_hc = h;
-                        my_sc = v;
-                    }
-                }
+                const int h = __reduce_add_sync(0xffffffffu, hc[t]);
+                if (out_t == t) my_hc = h;
             }
+            my_sc = warp_sum_scatter<TILE>(sc, lane);
         }
-        if (lane < nb) {
+        if ((lane & ((32 >> LG) - 1)) == 0 && out_t < nb) {
             float d;
-            if (ha.z | s_st[lane]) {
+            if (ha.z | s_st[out_t]) {
                 d = __int_as_float(0x7fc00000);
             } else {
-                const int n_b = (int)s_n[lane], m_b = (int)s_m[lane];
+                const int n_b = (int)s_n[out_t], m_b = (int)s_m[out_t];
                 const int nmax = max(n_a, n_b), mmax = max(m_a, m_b);
                 const float dn = nmax ? fmaf(p.cd, (float)(n_a + n_b - 2 * my_hn), p.ch * my_sn) / (float)nmax : 0.0f;
                 const float dc = mmax ? fmaf(p.cd, (float)(m_a + m_b - 2 * my_hc), p.ch * my_sc) / (float)mmax : 0.0f;
                 d = dn + dc;
             }
-            p.out[(size_t)a * p.ldo + b0 + lane] = d;
+            p.out[(size_t)a * p.ldo + b0 + out_t] = d;
         }
     }
 }
@@ -675,8 +889,14 @@ extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_
     int rc = allow_dynamic_smem(reinterpret_cast<const void *>(prepare_kernel), smem,
                                 "neat_distance_prepare: shared memory per block");
     if (rc) return rc;
-    const int threads = (a.N <= 64 && a.C <= 512) ? 128 : kPrepThreads;   // small genomes: more blocks per SM
-    prepare_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
+    a.pop = pop;
+    if (a.N <= kWarpMaxNodes && a.C <= kWarpMaxConns) {
+        const int blocks = (pop + kPrepWarpGenomes - 1) / kPrepWarpGenomes;
+        prepare_warp_kernel<<<blocks, 32 * kPrepWarpGenomes, 0, as_stream(stream)>>>(a);
+    } else {
+        const int threads = (a.N <= 64 && a.C <= 512) ? 128 : kPrepThreads;   // small genomes: more blocks per SM
+        prepare_kernel<<<pop, threads, smem, as_stream(stream)>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neat_distance_prepare: launch");
     return NEAT_OK;

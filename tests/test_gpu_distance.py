@@ -82,6 +82,57 @@ def test_gene_records(neat):
         np.testing.assert_array_equal(raw[g, off:off + 8 * m].view(np.uint64), pairs)
 
 
+def _records(neat, nodes, conns, I, O):
+    d = neat.dims(I, O, nodes.shape[1], conns.shape[1])
+    genes, st = neat.neat_distance_prepare(_dev(nodes), _dev(conns), d)
+    stride = neat.neat_gene_stride(d)
+    return genes.cpu().numpy()[: nodes.shape[0] * stride].reshape(nodes.shape[0], stride), st.cpu().numpy()
+
+
+def _written(rec):
+    """The bytes a gene record defines: the header, then for a valid record
+    the node keys with their padding, node attributes, pair keys and
+    connection attributes (the last few bytes of alignment are unwritten)."""
+    n, m, status = (int(x) for x in rec[:12].view(np.uint32))
+    if status:
+        return rec[:16]
+    return rec[:16 + (4 * n + 15) // 16 * 16 + 16 * n + 16 * m]
+
+
+def test_gene_record_forms_agree(neat):
+    """Genomes of at most 64 node rows and 256 connection rows are prepared
+    one warp each (keys sorted in registers), larger ones one block each
+    (keys sorted in shared memory): the same genomes padded past those
+    limits give the same record bytes and statuses.  Error genomes (a
+    duplicated key, a duplicated pair, a bad key), an empty genome and full
+    64 x 256 genomes included."""
+    p = _related(12, 90)
+    nodes, conns = p.nodes.copy(), p.conns.copy()
+    rn = np.flatnonzero(~np.isnan(nodes[5, :, 0]))
+    nodes[5, rn[1]] = nodes[5, rn[0]]
+    rc = np.flatnonzero(~np.isnan(conns[9, :, 0]))
+    conns[9, rc[1]] = conns[9, rc[0]]
+    nodes[13, rn[2], 0] = 1.5
+    nodes[20] = np.nan
+    conns[20] = np.nan
+    conns[21] = np.nan                                      # nodes only
+    full = W.random_dag_population(13, 40, 3, 2, 64, 256, hidden=lambda r: 59,
+                                   edges=lambda r, n: int(r.integers(200, 257)), acts=W.ALL_ACTS,
+                                   aggs=W.ALL_AGGS, p_disabled=0.3)
+    for (nd, cn, nmax, cmax) in ((nodes, conns, 100, 60), (full.nodes, full.conns, 65, 256),
+                                 (full.nodes, full.conns, 64, 300)):
+        warp, st_w = _records(neat, nd, cn, 3, 2)
+        block, st_b = _records(neat, _pad(nd, nmax), _pad(cn, cmax), 3, 2)
+        np.testing.assert_array_equal(st_w, st_b)
+        for g in range(nd.shape[0]):
+            np.testing.assert_array_equal(_written(warp[g]), _written(block[g]), err_msg=f"genome {g}")
+    assert (st_w == 0).all()
+    _, st = _records(neat, nodes, conns, 3, 2)
+    assert np.flatnonzero(st).tolist() == [5, 9, 13]
+    n_full = (~np.isnan(full.nodes[:, :, 0])).sum(1)
+    assert n_full.max() == 64 and (~np.isnan(full.conns[:, :, 0])).sum(1).max() > 200
+
+
 @pytest.mark.parametrize("cd,ch", [(1.0, 0.5), (2.0, 3.0)])
 def test_distances_match_oracle(neat, cd, ch):
     a = _related(2, 70)
