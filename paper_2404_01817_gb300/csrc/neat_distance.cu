@@ -534,6 +534,13 @@ __device__ __forceinline__ float conn_term(float2 x, float2 y)
     return fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
 }
 
+// v where keep, else +0 (a bit mask: the term is computed either way, with
+// no branch around it).
+__device__ __forceinline__ float masked(float v, bool keep)
+{
+    return __uint_as_float(__float_as_uint(v) & (0u - (uint32_t)keep));
+}
+
 __host__ __device__ constexpr int log2_tile(int t) { return t >= 16 ? 4 : t >= 8 ? 3 : t >= 4 ? 2 : t >= 2 ? 1 : 0; }
 
 // Warp totals of TILE per-lane values, one reduce-scatter: lane l ends with
@@ -704,7 +711,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                         const bool h = i != 0xffu;
                         const uint4 y = *reinterpret_cast<const uint4 *>(sm + noff[t] + (h ? i : 0u) * 16u);
                         hn[t] += h;
-                        sn[t] += h ? node_term(x, y) : 0.0f;
+                        sn[t] += masked(node_term(x, y), h);
                     }
                 } else {
 #pragma unroll
@@ -757,7 +764,7 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                         const bool h = i != 0xffu;
                         const float2 y = *reinterpret_cast<const float2 *>(sm + coff[t] + (h ? i : 0u) * 8u);
                         hc[t] += h;
-                        sc[t] += h ? conn_term(x, y) : 0.0f;
+                        sc[t] += masked(conn_term(x, y), h);
                     }
                 } else {
 #pragma unroll
