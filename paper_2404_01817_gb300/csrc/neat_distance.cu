@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_kernel(const PrepArgs a)
 // register e / 32 (registers R.. of v are left alone).  A compare-exchange
 // partner 32 j' or more positions away sits in another register of the same
 // lane; a nearer one in another lane at the same register.
-template <int R, int NR>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[NR], int lane)
+template <int R, typename T, int NR>
+__device__ __forceinline__ void warp_bitonic(T (&v)[NR], int lane)
 {
     static_assert(R <= NR, "registers");
     constexpr int n2 = 32 * R;
@@ -197,7 +197,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[NR], int la
                 for (int r = 0; r < R; ++r) {
                     if (!(r & jr)) {
                         const bool up = (((r << 5) | lane) & k) == 0;
-                        const unsigned long long x = v[r], y = v[r | jr];
+                        const T x = v[r], y = v[r | jr];
                         if ((x > y) == up) {
                             v[r] = y;
                             v[r | jr] = x;
@@ -210,8 +210,8 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[NR], int la
             const bool lower = (lane & j) == 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const unsigned long long x = v[r];
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+                const T x = v[r];
+                const T y = __shfl_xor_sync(0xffffffffu, x, j);
                 const bool up = (((r << 5) | lane) & k) == 0;
                 // in an ascending run the lower position keeps the smaller key
                 v[r] = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
@@ -220,8 +220,8 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[NR], int la
     }
 }
 
-template <int NR>
-__device__ __forceinline__ void warp_bitonic_any(unsigned long long (&v)[NR], int regs, int lane)
+template <typename T, int NR>
+__device__ __forceinline__ void warp_bitonic_any(T (&v)[NR], int regs, int lane)
 {
     if (regs <= 1) warp_bitonic<1>(v, lane);
     else if (regs <= 2) warp_bitonic<(NR < 2 ? NR : 2)>(v, lane);
@@ -231,17 +231,16 @@ __device__ __forceinline__ void warp_bitonic_any(unsigned long long (&v)[NR], in
 
 // True in some lane when two of the first `count` sorted keys agree in the
 // bits above `shift`.
-template <int NR>
-__device__ __forceinline__ bool warp_has_equal_neighbours(const unsigned long long (&v)[NR], int regs, int count,
-                                                          int shift, int lane)
+template <typename T, int NR>
+__device__ __forceinline__ bool warp_has_equal_neighbours(const T (&v)[NR], int regs, int count, int shift, int lane)
 {
     bool dup = false;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         if (r < regs) {
-            const unsigned long long up1 = __shfl_up_sync(0xffffffffu, v[r], 1);
-            const unsigned long long last = r ? __shfl_sync(0xffffffffu, v[r ? r - 1 : 0], 31) : 0ull;
-            const unsigned long long prev = lane ? up1 : last;
+            const T up1 = __shfl_up_sync(0xffffffffu, v[r], 1);
+            const T last = r ? __shfl_sync(0xffffffffu, v[r ? r - 1 : 0], 31) : T(0);
+            const T prev = lane ? up1 : last;
             const int e = (r << 5) | lane;
             if (e >= 1 && e < count && (v[r] >> shift) == (prev >> shift)) dup = true;
         }
@@ -264,6 +263,7 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
     uint32_t st = 0;
     // present rows, compacted in row order (the sort makes the order moot)
     int n = 0, m = 0;
+    uint32_t wide = 0;   // key bits at or above 2^12 in any connection
     for (int base = 0; base < a.N; base += 32) {
         const int r = base + lane;
         bool ok = false;
@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
                     ok = true;
                     const unsigned long long pair = ((unsigned long long)(uint32_t)row.x << 24) | (uint32_t)row.y;
                     v = (pair << 13) | (unsigned)c;
+                    wide |= ((uint32_t)row.x | (uint32_t)row.y) >> 12;
                 } else {
                     st |= NEAT_G_BADKEY;
                 }
@@ -304,23 +305,46 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
         m += __popc(b);
     }
     __syncwarp();
-    // n <= 64 and m <= 256 present rows: 2 and 8 registers a lane at most
-    unsigned long long vn[2], vc[8];
+    // n <= 64 and m <= 256 present rows: 2 and 8 registers a lane at most.
+    // Sort keys in 32 bits where they fit, in the order of the 64-bit ones:
+    // node key << 6 | row (keys below 2^24, rows below 64), and for
+    // connections whose keys are all below 2^12, in << 20 | out << 8 | row.
+    uint32_t vn[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int e = (r << 5) | lane;
-        vn[r] = e < n ? nk[e] : ~0ull;
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int e = (r << 5) | lane;
-        vc[r] = e < m ? ck[e] : ~0ull;
+        vn[r] = e < n ? (uint32_t)(nk[e] >> 32) << 6 | (uint32_t)(nk[e] & 63u) : 0xffffffffu;
     }
     const int rn = (n + 31) >> 5, rc = (m + 31) >> 5;   // registers in use (0 for none)
     warp_bitonic_any(vn, rn, lane);
-    warp_bitonic_any(vc, rc, lane);
-    if (warp_has_equal_neighbours(vn, rn, n, 32, lane)) st |= NEAT_G_DUPKEY;
-    if (warp_has_equal_neighbours(vc, rc, m, 13, lane)) st |= NEAT_G_DUPCONN;
+    if (warp_has_equal_neighbours(vn, rn, n, 6, lane)) st |= NEAT_G_DUPKEY;
+    const bool narrow = __reduce_or_sync(0xffffffffu, wide) == 0u;
+    unsigned long long vc[8];
+    if (narrow) {
+        uint32_t v32[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = (r << 5) | lane;
+            const unsigned long long v = e < m ? ck[e] : 0ull;
+            const uint32_t in = (uint32_t)(v >> 37), out = (uint32_t)(v >> 13) & 0xfffu;
+            v32[r] = e < m ? in << 20 | out << 8 | (uint32_t)(v & 0xffu) : 0xffffffffu;
+        }
+        warp_bitonic_any(v32, rc, lane);
+        if (warp_has_equal_neighbours(v32, rc, m, 8, lane)) st |= NEAT_G_DUPCONN;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const unsigned long long pair = (unsigned long long)(v32[r] >> 20) << 24 | ((v32[r] >> 8) & 0xfffu);
+            vc[r] = pair << 13 | (v32[r] & 0xffu);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = (r << 5) | lane;
+            vc[r] = e < m ? ck[e] : ~0ull;
+        }
+        warp_bitonic_any(vc, rc, lane);
+        if (warp_has_equal_neighbours(vc, rc, m, 13, lane)) st |= NEAT_G_DUPCONN;
+    }
     st = __reduce_or_sync(0xffffffffu, st);
     uint8_t *rec = a.out + (size_t)g * a.stride;
     if (st) {
@@ -337,8 +361,8 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
     for (int r = 0; r < 2; ++r) {
         const int e = (r << 5) | lane;
         if (e < n) {
-            const float *row = nd + (size_t)(vn[r] & 0xffffffffu) * 5;
-            okey[e] = (uint32_t)(vn[r] >> 32);
+            const float *row = nd + (size_t)(vn[r] & 63u) * 5;
+            okey[e] = vn[r] >> 6;
             oattr[e] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
                                   __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
         }

@@ -105,7 +105,8 @@ def test_gene_record_forms_agree(neat):
     (keys sorted in shared memory): the same genomes padded past those
     limits give the same record bytes and statuses.  Error genomes (a
     duplicated key, a duplicated pair, a bad key), an empty genome and full
-    64 x 256 genomes included."""
+    64 x 256 genomes included, with keys below 2^12 (32-bit sort keys in the
+    warp form) and above (64-bit ones)."""
     p = _related(12, 90)
     nodes, conns = p.nodes.copy(), p.conns.copy()
     rn = np.flatnonzero(~np.isnan(nodes[5, :, 0]))
@@ -119,8 +120,11 @@ def test_gene_record_forms_agree(neat):
     full = W.random_dag_population(13, 40, 3, 2, 64, 256, hidden=lambda r: 59,
                                    edges=lambda r, n: int(r.integers(200, 257)), acts=W.ALL_ACTS,
                                    aggs=W.ALL_AGGS, p_disabled=0.3)
-    for (nd, cn, nmax, cmax) in ((nodes, conns, 100, 60), (full.nodes, full.conns, 65, 256),
-                                 (full.nodes, full.conns, 64, 300)):
+    wide_n, wide_c = full.nodes.copy(), full.conns.copy()    # keys past 2^12: 64-bit sort keys
+    wide_n[:, :, 0] += 5000.0
+    wide_c[:, :, :2] += 5000.0
+    for (nd, cn, nmax, cmax) in ((nodes, conns, 100, 60), (wide_n, wide_c, 65, 256),
+                                 (full.nodes, full.conns, 65, 256), (full.nodes, full.conns, 64, 300)):
         warp, st_w = _records(neat, nd, cn, 3, 2)
         block, st_b = _records(neat, _pad(nd, nmax), _pad(cn, cmax), 3, 2)
         np.testing.assert_array_equal(st_w, st_b)
