@@ -24,7 +24,7 @@
 //    them in one of three ways: for small genomes (at most 255 node and 255
 //    connection genes) one open-addressing table per gene kind over the
 //    union of the tile's keys, each entry holding the key's row index in
-//    every staged record (one byte per record, 0xFF where absent), so a gene
+//    every staged record (one byte per record: row + 1, 0 where absent), so a gene
 //    is probed once for the whole tile; otherwise one hash table per record;
 //    records too large for tables are searched by binary search in their
 //    sorted keys.  Its warps stream a-genomes from
@@ -472,13 +472,13 @@ __device__ __forceinline__ int conn_lookup(const unsigned long long *tab, uint32
 // Union tables (kUnion) of 16-byte entries: node entries {key, row indices
 // in records 0-3, in records 4-7, unused}, connection entries {pair (64
 // bits), row indices in records 0-3, in records 4-7}, one index byte per
-// staged record.  Every byte starts at 0xFF: a free entry has key 0xFFFFFFFF
-// (keys are below 2^24) or pair ~0 (pairs have 48 bits), and index 0xFF
-// means the record lacks the gene.  Linear probing; capacities are powers of
-// two above 1.25x the largest union a tile can have, so a probe sequence
-// always reaches a free entry.  Rows of one record are distinct per key
-// (duplicates make an error record, which holds no genes), so each index
-// byte has one writer.
+// staged record holding row + 1 (rows 0-254), 0 where the record lacks the
+// gene.  A free entry has key 0xFFFFFFFF (keys are below 2^24) or pair ~0
+// (pairs have 48 bits) and zero index bytes.  Linear probing; capacities
+// are powers of two above 1.25x the largest union a tile can have, so a
+// probe sequence always reaches a free entry.  Rows of one record are
+// distinct per key (duplicates make an error record, which holds no genes),
+// so each index byte has one writer.
 constexpr int kUnionMaxTile = 8;
 
 __device__ __forceinline__ void union_insert_node(uint4 *tab, uint32_t lg, uint32_t key, int t, uint32_t row)
@@ -488,7 +488,7 @@ __device__ __forceinline__ void union_insert_node(uint4 *tab, uint32_t lg, uint3
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const uint32_t old = atomicCAS(&tab[s].x, 0xffffffffu, key);
         if (old == 0xffffffffu || old == key) {
-            reinterpret_cast<unsigned char *>(tab + s)[4 + t] = (unsigned char)row;
+            reinterpret_cast<unsigned char *>(tab + s)[4 + t] = (unsigned char)(row + 1u);
             return;
         }
         s = (s + 1u) & mask;
@@ -503,15 +503,15 @@ __device__ __forceinline__ void union_insert_conn(uint4 *tab, uint32_t lg, unsig
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long *>(tab + s), kEmpty, pair);
         if (old == kEmpty || old == pair) {
-            reinterpret_cast<unsigned char *>(tab + s)[8 + t] = (unsigned char)row;
+            reinterpret_cast<unsigned char *>(tab + s)[8 + t] = (unsigned char)(row + 1u);
             return;
         }
         s = (s + 1u) & mask;
     }
 }
 
-// The index bytes of `key` (records 0-3, records 4-7); all 0xFF when no
-// staged record has it.
+// The index bytes of `key` (records 0-3, records 4-7); all 0 when no staged
+// record has it.
 __device__ __forceinline__ uint2 union_find_node(const uint4 *tab, uint32_t lg, uint32_t key)
 {
     const uint32_t mask = (1u << lg) - 1u;
@@ -522,7 +522,7 @@ __device__ __forceinline__ uint2 union_find_node(const uint4 *tab, uint32_t lg, 
         if (e.x == 0xffffffffu) break;
         s = (s + 1u) & mask;
     }
-    return make_uint2(~0u, ~0u);
+    return make_uint2(0u, 0u);
 }
 
 __device__ __forceinline__ uint2 union_find_conn(const uint4 *tab, uint32_t lg, unsigned long long pair)
@@ -535,11 +535,11 @@ __device__ __forceinline__ uint2 union_find_conn(const uint4 *tab, uint32_t lg, 
         if (e.y == 0xffffffffu) break;
         s = (s + 1u) & mask;
     }
-    return make_uint2(~0u, ~0u);
+    return make_uint2(0u, 0u);
 }
 
-// Row of record t among the index bytes of a union entry (t a constant
-// after unrolling).
+// Row + 1 in record t (0 where absent) among the index bytes of a union
+// entry (t a constant after unrolling).
 __device__ __forceinline__ uint32_t union_row(uint2 ix, int t)
 {
     return ((t < 4 ? ix.x : ix.y) >> (8 * (t & 3))) & 0xffu;
@@ -558,11 +558,11 @@ __device__ __forceinline__ float conn_term(float2 x, float2 y)
     return fabsf(x.x - y.x) + ((x.y != y.y) ? 1.0f : 0.0f);
 }
 
-// v where keep, else +0 (a bit mask: the term is computed either way, with
-// no branch around it).
-__device__ __forceinline__ float masked(float v, bool keep)
+// v where the mask is all ones, +0 where it is 0 (the term is computed
+// either way, with no branch around it).
+__device__ __forceinline__ float masked(float v, uint32_t mask)
 {
-    return __uint_as_float(__float_as_uint(v) & (0u - (uint32_t)keep));
+    return __uint_as_float(__float_as_uint(v) & mask);
 }
 
 __host__ __device__ constexpr int log2_tile(int t) { return t >= 16 ? 4 : t >= 8 ? 3 : t >= 4 ? 2 : t >= 2 ? 1 : 0; }
@@ -597,8 +597,10 @@ __device__ __forceinline__ float warp_sum_scatter(const float (&v)[TILE], int la
     return w[0];
 }
 
+// Three blocks per SM at the Ant size (shared memory allows no more): the
+// hint lets the union form keep its per-record offsets and sums in registers.
 template <int MODE, int TILE>
-__global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p)
+__global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArgs p)
 {
     static_assert(MODE != kUnion || TILE <= kUnionMaxTile, "union entries hold 8 index bytes");
     extern __shared__ __align__(16) unsigned char sm[];
@@ -636,7 +638,9 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         // after the tile's records, outside the copied bytes
         uint4 *u = reinterpret_cast<uint4 *>(sm + p.union_off);
         const uint32_t entries = (1u << p.lgn) + (1u << p.lgc);
-        for (uint32_t i = tid; i < entries; i += kDistThreads) u[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        const uint32_t node_entries = 1u << p.lgn;
+        for (uint32_t i = tid; i < entries; i += kDistThreads)
+            u[i] = i < node_entries ? make_uint4(~0u, 0u, 0u, 0u) : make_uint4(~0u, ~0u, 0u, 0u);
     }
     __syncthreads();
     if (!mbar_wait(bar, 0)) failed = 1;
@@ -691,14 +695,16 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
         }
     }
     __syncthreads();
-    // byte offsets of every staged record's node and connection attributes
-    // (0 past the tile: the union form reads a row of every record, and
-    // discards the rows of records that lack the gene)
+    // byte offsets of every staged record's row "-1" of node and connection
+    // attributes (the union form reads row b - 1 of every record for index
+    // byte b and discards the rows of records that lack the gene, b = 0:
+    // those reads land in the record's 16 bytes before its attributes, or
+    // at the start of shared memory past the tile)
     uint32_t noff[TILE], coff[TILE];
 #pragma unroll
     for (int t = 0; t < TILE; ++t) {
-        noff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_nattr[t] : 0u;
-        coff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_cattr[t] : 0u;
+        noff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_nattr[t] - 16u : 0u;
+        coff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_cattr[t] - 8u : 0u;
     }
     constexpr int LG = log2_tile(TILE);
     const int out_t = lane >> (5 - LG);              // the representative whose totals this lane ends with
@@ -731,11 +737,11 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
 #pragma unroll
                     for (int t = 0; t < TILE; ++t) {
                         // partial sums are >= +0, so adding +0 for an absent gene changes no bit
-                        const uint32_t i = union_row(ix, t);
-                        const bool h = i != 0xffu;
-                        const uint4 y = *reinterpret_cast<const uint4 *>(sm + noff[t] + (h ? i : 0u) * 16u);
-                        hn[t] += h;
-                        sn[t] += masked(node_term(x, y), h);
+                        const uint32_t b = union_row(ix, t);
+                        const uint32_t keep = (uint32_t)(-(int32_t)b >> 31);   // all ones where present
+                        const uint4 y = *reinterpret_cast<const uint4 *>(sm + noff[t] + b * 16u);
+                        hn[t] -= (int)keep;
+                        sn[t] += masked(node_term(x, y), keep);
                     }
                 } else {
 #pragma unroll
@@ -784,11 +790,11 @@ __global__ void __launch_bounds__(kDistThreads) distance_kernel(const DistArgs p
                                                      p.lgc, key);
 #pragma unroll
                     for (int t = 0; t < TILE; ++t) {
-                        const uint32_t i = union_row(ix, t);
-                        const bool h = i != 0xffu;
-                        const float2 y = *reinterpret_cast<const float2 *>(sm + coff[t] + (h ? i : 0u) * 8u);
-                        hc[t] += h;
-                        sc[t] += masked(conn_term(x, y), h);
+                        const uint32_t b = union_row(ix, t);
+                        const uint32_t keep = (uint32_t)(-(int32_t)b >> 31);
+                        const float2 y = *reinterpret_cast<const float2 *>(sm + coff[t] + b * 8u);
+                        hc[t] -= (int)keep;
+                        sc[t] += masked(conn_term(x, y), keep);
                     }
                 } else {
 #pragma unroll
