@@ -27,13 +27,13 @@
 //    every staged record (one byte per record: row + 1, 0 where absent), so a gene
 //    is probed once for the whole tile; otherwise one hash table per record;
 //    records too large for tables are searched by binary search in their
-//    sorted keys.  Its warps stream a-genomes from
-//    global memory (L2-resident across blocks): lane l loads a's genes l,
-//    l+32, ... once each and looks every one up in all staged b-records
-//    (independent lookups in flight, per-representative sums in registers);
-//    the counts and sums are reduced across the warp along a fixed tree, so
-//    every result is a function of the two genomes alone, whichever lookup
-//    finds the homologous gene.
+//    sorted keys.  Its warps stream a-genomes from global memory
+//    (L2-resident across blocks), two per warp: lane l of a half-warp loads
+//    a's genes l, l+16, ... once each and looks every one up in all staged
+//    b-records (independent lookups in flight, per-representative sums in
+//    registers); the counts and sums are reduced across the half-warp along
+//    a fixed tree, so every result is a function of the two genomes alone,
+//    whichever form or lookup finds the homologous gene.
 //  * neat_speciate: one warp per genome scans its distance row for the
 //    nearest representative under the threshold.
 #include <algorithm>
@@ -567,33 +567,33 @@ __device__ __forceinline__ float masked(float v, uint32_t mask)
 
 __host__ __device__ constexpr int log2_tile(int t) { return t >= 16 ? 4 : t >= 8 ? 3 : t >= 4 ? 2 : t >= 2 ? 1 : 0; }
 
-// Warp totals of TILE per-lane values, one reduce-scatter: lane l ends with
-// the total of v[l >> (5 - log2 TILE)].  The first log2 TILE exchange steps
-// (offsets 16, 8, ...) each send half of the lane's remaining values to the
-// partner and keep the other half, the rest add whole values; lanes are
-// paired in the order 16, 8, 4, 2, 1 throughout, so every total is the sum
-// tree of a butterfly reduction of that value alone.
-template <int TILE>
-__device__ __forceinline__ float warp_sum_scatter(const float (&v)[TILE], int lane)
+// Half-warp totals of TILE per-lane values, one reduce-scatter: lane l ends
+// with its half's total of v[(l & 15) >> (4 - log2 TILE)].  The first
+// log2 TILE exchange steps (offsets 8, 4, ...) each send half of the lane's
+// remaining values to the partner and keep the other half, the rest add
+// whole values; lanes are paired in the order 8, 4, 2, 1 throughout, so
+// every total is the sum tree of a butterfly reduction of that value alone.
+template <int TILE, typename T>
+__device__ __forceinline__ T half_sum_scatter(const T (&v)[TILE], int lane)
 {
     constexpr int LG = log2_tile(TILE);
     static_assert((1 << LG) == TILE, "TILE is a power of two");
-    float w[TILE];
+    T w[TILE];
 #pragma unroll
     for (int i = 0; i < TILE; ++i) w[i] = v[i];
 #pragma unroll
     for (int s = 0; s < LG; ++s) {
-        const int o = 16 >> s, half = TILE >> (s + 1);
+        const int o = 8 >> s, half = TILE >> (s + 1);
         const bool hi = (lane & o) != 0;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
-            const float send = hi ? w[i] : w[i + half];
-            const float keep = hi ? w[i + half] : w[i];
+            const T send = hi ? w[i] : w[i + half];
+            const T keep = hi ? w[i + half] : w[i];
             w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
 #pragma unroll
-    for (int o = 16 >> LG; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    for (int o = 8 >> LG; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
     return w[0];
 }
 
@@ -707,13 +707,19 @@ __global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArg
         coff[t] = t < nb ? (uint32_t)t * p.slot_bytes + s_cattr[t] - 8u : 0u;
     }
     constexpr int LG = log2_tile(TILE);
-    const int out_t = lane >> (5 - LG);              // the representative whose totals this lane ends with
-    for (int a = a_begin + warp; a < a_end; a += kDistWarps) {
-        const uint8_t *ra = p.a + (size_t)a * p.stride;
-        const uint4 ha = __ldg(reinterpret_cast<const uint4 *>(ra));
+    const int half = lane >> 4, hl = lane & 15;
+    const int out_t = hl >> (4 - LG);                // the representative whose totals this lane ends with
+    // two a-genomes per warp, one per half-warp (16 lanes fit the ~50 node
+    // genes of a small genome better than 32)
+    for (int a0 = a_begin + 2 * warp; a0 < a_end; a0 += 2 * kDistWarps) {
+        const int a = a0 + half;
+        const bool live = a < a_end;
+        const uint8_t *ra = p.a + (size_t)(live ? a : a0) * p.stride;
+        uint4 ha = __ldg(reinterpret_cast<const uint4 *>(ra));
+        if (!live) ha = make_uint4(0u, 0u, 0u, kGeneHeaderBytes);   // no genes: the half idles to the reductions
         const int n_a = (int)ha.x, m_a = (int)ha.y;
         const GeneLayout La = gene_layout(ha.x, ha.y);
-        // lane l ends up with the totals of representative out_t = l >> (5 - log2 TILE)
+        // lane l ends up with its half's totals of representative out_t
         int my_hn = 0, my_hc = 0;
         float my_sn = 0.0f, my_sc = 0.0f;
         {
@@ -728,7 +734,7 @@ __global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArg
             }
             const uint32_t *ka = reinterpret_cast<const uint32_t *>(ra + La.nkey);
             const uint4 *aa = reinterpret_cast<const uint4 *>(ra + La.nattr);
-            for (int j = lane; j < n_a; j += 32) {
+            for (int j = hl; j < n_a; j += 16) {
                 const uint32_t key = __ldg(ka + j);
                 const uint4 x = __ldg(aa + j);
                 if constexpr (MODE == kUnion) {
@@ -764,12 +770,8 @@ __global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArg
                     }
                 }
             }
-#pragma unroll
-            for (int t = 0; t < TILE; ++t) {
-                const int h = __reduce_add_sync(0xffffffffu, hn[t]);
-                if (out_t == t) my_hn = h;
-            }
-            my_sn = warp_sum_scatter<TILE>(sn, lane);
+            my_hn = half_sum_scatter<TILE>(hn, lane);
+            my_sn = half_sum_scatter<TILE>(sn, lane);
         }
         {
             // connection genes, the same way
@@ -782,7 +784,7 @@ __global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArg
             }
             const unsigned long long *ka = reinterpret_cast<const unsigned long long *>(ra + La.ckey);
             const float2 *aa = reinterpret_cast<const float2 *>(ra + La.cattr);
-            for (int j = lane; j < m_a; j += 32) {
+            for (int j = hl; j < m_a; j += 16) {
                 const unsigned long long key = __ldg(ka + j);
                 const float2 x = __ldg(aa + j);
                 if constexpr (MODE == kUnion) {
@@ -818,14 +820,10 @@ __global__ void __launch_bounds__(kDistThreads, 3) distance_kernel(const DistArg
                     }
                 }
             }
-#pragma unroll
-            for (int t = 0; t < TILE; ++t) {
-                const int h = __reduce_add_sync(0xffffffffu, hc[t]);
-                if (out_t == t) my_hc = h;
-            }
-            my_sc = warp_sum_scatter<TILE>(sc, lane);
+            my_hc = half_sum_scatter<TILE>(hc, lane);
+            my_sc = half_sum_scatter<TILE>(sc, lane);
         }
-        if ((lane & ((32 >> LG) - 1)) == 0 && out_t < nb) {
+        if (live && (hl & ((16 >> LG) - 1)) == 0 && out_t < nb) {
             float d;
             if (ha.z | s_st[out_t]) {
                 d = __int_as_float(0x7fc00000);
@@ -1017,7 +1015,7 @@ extern "C" int neat_distance(const void *genes_a, int32_t pop_a, const void *gen
     const int resident = std::max(1, std::min(3, (int)(smem_sm / (smem + 1024u))));
     const long want_x = std::max<long>(1, ((long)sms * resident + tiles - 1) / tiles);
     long apb = (pop_a + want_x - 1) / want_x;
-    apb = std::max<long>(kDistWarps, (apb + kDistWarps - 1) / kDistWarps * kDistWarps);
+    apb = std::max<long>(2 * kDistWarps, (apb + 2 * kDistWarps - 1) / (2 * kDistWarps) * (2 * kDistWarps));
     p.a_per_block = (int)std::min<long>(apb, 1L << 30);
     const long gx = (pop_a + p.a_per_block - 1) / p.a_per_block;
     using Kern = void (*)(DistArgs);
