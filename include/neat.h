@@ -574,7 +574,9 @@ NEAT_API int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat_d
  * aggregation, activation; connection: enabled, weight; its lowest such row)
  * when words_dev[k][row] (words_dev[k][max_nodes + row] for connections),
  * uint32 [n_children][max_nodes + max_conns], is >= 2^31.  Outputs
- * [n_children][...] must not overlap the inputs.  Errors: NEAT_EINVAL, NEAT_ECUDA. */
+ * [n_children][...] must not overlap the inputs.  A child with a parent
+ * index outside [0, pop) is written empty (every row NaN).  Errors:
+ * NEAT_EINVAL, NEAT_ECUDA. */
 NEAT_API int neat_crossover(const float *nodes_dev, const float *conns_dev, int32_t pop, neat_dims d,
                             const int32_t *parents_dev, int32_t n_children, const uint32_t *words_dev,
                             float *nodes_out_dev, float *conns_out_dev, void *stream);

@@ -313,6 +313,15 @@ struct CrossArgs {
     int pop, K, N, C, Np2, Cp2;
 };
 
+// A child whose parent index lies outside [0, pop) is written empty (every
+// row NaN) by threads i, i + step, ...
+__device__ __forceinline__ void write_empty_child(float *no, float4 *co, int N, int C, int lane, int step)
+{
+    for (int e = lane; e < N * 5; e += step) no[e] = __int_as_float(0x7fc00000);
+    const float q = __int_as_float(0x7fc00000);
+    for (int c = lane; c < C; c += step) co[c] = make_float4(q, q, q, q);
+}
+
 __global__ void __launch_bounds__(kEvoThreads) crossover_kernel(const CrossArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -322,6 +331,11 @@ __global__ void __launch_bounds__(kEvoThreads) crossover_kernel(const CrossArgs 
     const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int N = a.N, C = a.C;
     const int p1 = __ldg(a.parents + 2 * k), p2 = __ldg(a.parents + 2 * k + 1);
+    if (p1 < 0 || p1 >= a.pop || p2 < 0 || p2 >= a.pop) {
+        write_empty_child(a.nodes_out + (size_t)k * N * 5, reinterpret_cast<float4 *>(a.conns_out + (size_t)k * C * 4),
+                          N, C, tid, nt);
+        return;
+    }
     const float *n1 = a.nodes + (size_t)p1 * N * 5, *n2 = a.nodes + (size_t)p2 * N * 5;
     const float *c1 = a.conns + (size_t)p1 * C * 4, *c2 = a.conns + (size_t)p2 * C * 4;
     float *no = a.nodes_out + (size_t)k * N * 5;

@@ -177,6 +177,39 @@ def test_crossover_matches_oracle_bit_for_bit(neat):
     np.testing.assert_array_equal(gn.cpu().numpy()[:20].view(np.uint32), p.nodes[parents[:20, 0]].view(np.uint32))
 
 
+def test_crossover_launch_shapes_and_bad_parents(neat):
+    """Genomes of at most 64 node rows and 256 connection rows cross with
+    128 threads per child, larger ones with 256: the same parents padded to
+    100 node rows (words moved with the rows) give the same children, bit
+    for bit with the oracle.  A parent index outside [0, pop) gives an empty
+    child; the other children are unaffected."""
+    p = W.related_population(20, 300, 3, 2, 24, 60, ancestor_hidden=6, ancestor_edges=20, new_nodes=6,
+                             new_conns=12, key_pool=10)
+    rng = np.random.default_rng(21)
+    parents = rng.integers(0, 300, size=(333, 2)).astype(np.int32)
+    words = rng.integers(0, 2**32, size=(333, 84), dtype=np.uint64).astype(np.uint32)
+    on, oc = oracle.crossover(p.nodes, p.conns, parents, words)
+    bad = parents.copy()
+    bad[5, 0], bad[6, 1], bad[7, 1] = 300, -1, 1 << 30
+    for nmax in (24, 100):
+        nodes = np.full((300, nmax, 5), np.nan, np.float32)
+        nodes[:, :24] = p.nodes
+        pw = np.zeros((333, nmax + 60), np.uint32)
+        pw[:, :24], pw[:, nmax:] = words[:, :24], words[:, 24:]
+        d = neat.dims(3, 2, nmax, 60)
+        gn, gc = neat.neat_crossover(_dev(nodes), _dev(p.conns), d, _dev(parents), _dev(pw.view(np.int32)))
+        gn = gn.cpu().numpy()
+        assert np.isnan(gn[:, 24:]).all()
+        np.testing.assert_array_equal(gn[:, :24].view(np.uint32), on.view(np.uint32), err_msg=f"nmax={nmax}")
+        np.testing.assert_array_equal(gc.cpu().numpy().view(np.uint32), oc.view(np.uint32), err_msg=f"nmax={nmax}")
+        bn, bc = neat.neat_crossover(_dev(nodes), _dev(p.conns), d, _dev(bad), _dev(pw.view(np.int32)))
+        bn, bc = bn.cpu().numpy(), bc.cpu().numpy()
+        assert np.isnan(bn[5:8]).all() and np.isnan(bc[5:8]).all()
+        keep = np.r_[0:5, 8:333]
+        np.testing.assert_array_equal(bn[keep, :24].view(np.uint32), on[keep].view(np.uint32))
+        np.testing.assert_array_equal(bc[keep].view(np.uint32), oc[keep].view(np.uint32))
+
+
 def test_random_words(neat):
     import torch
     a = torch.empty(1 << 20, dtype=torch.int32, device="cuda")
