@@ -632,7 +632,7 @@ def run_distance(args, R=64):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    n_rep = max(args.steps, 300)
+    n_rep = max(args.steps, 1500)                     # ~0.25 s: a dozen clock samples
     with ClockSampler(0) as clocks:
         ms = timed_events(step, n_rep, stream)
     parts = []
@@ -741,7 +741,7 @@ def run_evolve(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    n_rep = max(args.steps, 400)
+    n_rep = max(args.steps, 800)                      # ~0.25 s: a dozen clock samples
     with ClockSampler(0) as clocks:
         ms = timed_events(step, n_rep, stream)
     parts = []
