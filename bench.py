@@ -697,7 +697,8 @@ def run_distance(args, R=64):
 def run_evolve(args):
     """One generation of variation for 10000 Ant-shaped genomes in
     mid-evolution (27 in, 8 out, max 50 nodes / 200 conns): random words and
-    normals (Philox), 10000 crossovers of random parent pairs, mutation with
+    normals (Philox; the mutation's on a second stream beside the
+    crossover), 10000 crossovers of random parent pairs, mutation with
     the appendix's Brax settings (node_add 0.2, conn_add 0.4, bias and weight
     perturbation 0.5 at rates 0.7 / 0.8, replacement 0.1; feedforward
     check), and the transform of the children (ready for evaluation)."""
@@ -729,17 +730,26 @@ def run_evolve(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     gen = [0]
 
+    # the mutation's random inputs on a second stream, beside the crossover
+    # (they do not depend on it); the mutation waits for both
+    side = torch.cuda.Stream(dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+
     def step(record=False):
         g = gen[0]
         gen[0] += 1
         if record:
             ev[0].record(stream)
+        fork.record(stream)
+        side.wait_event(fork)
+        neat.neat_fill_words(11, 3 * g + 1, mwords, stream=side)
+        neat.neat_fill_normal(11, g, normals, stream=side)
+        join.record(side)
         neat.neat_fill_words(11, 3 * g, xwords, stream=stream)
-        neat.neat_fill_words(11, 3 * g + 1, mwords, stream=stream)
-        neat.neat_fill_normal(11, g, normals, stream=stream)
         if record:
             ev[1].record(stream)
         neat.neat_crossover(nodes, conns, d, parents, xwords, child_n, child_c, stream=stream)
+        stream.wait_event(join)
         if record:
             ev[2].record(stream)
         neat.neat_mutate(child_n, child_c, d, cfg, mwords, normals, keys, stream=stream)
@@ -760,7 +770,7 @@ def run_evolve(args):
         torch.cuda.synchronize()
         parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
     comp = {k: statistics.median(p[i] for p in parts)
-            for i, k in enumerate(("random_inputs", "crossover", "mutate", "transform"))}
+            for i, k in enumerate(("crossover_words", "crossover_and_mutation_inputs", "mutate", "transform"))}
     assert (status.cpu().numpy() & 0xFF == 0).all(), "children must stay valid and acyclic"
     t = statistics.median(ms) / 1e3
     # the mutation kernel's bytes: the children's tensors read and written, its random inputs read
