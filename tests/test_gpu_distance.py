@@ -169,13 +169,16 @@ def test_random_dag_populations_and_wide_genomes(neat):
 
 def test_tiling_does_not_change_bits(neat):
     """A column of the distance matrix has the same bits whichever tile of
-    representatives, and whichever block of a-genomes, computes it."""
+    representatives, and whichever block of a-genomes, computes it: 1 to 5
+    and 9 representatives (tiles of 1, 2, 4 and 8 records, full and partial)
+    against a run over 40."""
     p = _related(6, 300)
     d, genes, _ = _prepare(neat, p.nodes, p.conns)
     full = neat.neat_distance(genes, 300, genes, 40, d, 1.0, 0.5).cpu().numpy()
     stride = neat.neat_gene_stride(d)
-    part = neat.neat_distance(genes[7 * stride:], 290, genes[5 * stride:], 9, d, 1.0, 0.5).cpu().numpy()
-    np.testing.assert_array_equal(part, full[7:297, 5:14])
+    for nb in (1, 2, 3, 4, 5, 9):
+        part = neat.neat_distance(genes[7 * stride:], 290, genes[5 * stride:], nb, d, 1.0, 0.5).cpu().numpy()
+        np.testing.assert_array_equal(part, full[7:297, 5:5 + nb], err_msg=f"{nb} representatives")
 
 
 def _pad(a, rows):
