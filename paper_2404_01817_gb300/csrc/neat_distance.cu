@@ -319,7 +319,14 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
     warp_bitonic_any(vn, rn, lane);
     if (warp_has_equal_neighbours(vn, rn, n, 6, lane)) st |= NEAT_G_DUPKEY;
     const bool narrow = __reduce_or_sync(0xffffffffu, wide) == 0u;
-    unsigned long long vc[8];
+    // the sorted keys go back to the warp's shared arrays (the register
+    // arrays end with the sort)
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int e = (r << 5) | lane;
+        if (e < n) nk[e] = vn[r];
+    }
     if (narrow) {
         uint32_t v32[8];
 #pragma unroll
@@ -331,12 +338,15 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
         }
         warp_bitonic_any(v32, rc, lane);
         if (warp_has_equal_neighbours(v32, rc, m, 8, lane)) st |= NEAT_G_DUPCONN;
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
+            const int e = (r << 5) | lane;
             const unsigned long long pair = (unsigned long long)(v32[r] >> 20) << 24 | ((v32[r] >> 8) & 0xfffu);
-            vc[r] = pair << 13 | (v32[r] & 0xffu);
+            if (e < m) ck[e] = pair << 13 | (v32[r] & 0xffu);
         }
     } else {
+        unsigned long long vc[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int e = (r << 5) | lane;
@@ -344,7 +354,14 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
         }
         warp_bitonic_any(vc, rc, lane);
         if (warp_has_equal_neighbours(vc, rc, m, 13, lane)) st |= NEAT_G_DUPCONN;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = (r << 5) | lane;
+            if (e < m) ck[e] = vc[r];
+        }
     }
+    __syncwarp();
     st = __reduce_or_sync(0xffffffffu, st);
     uint8_t *rec = a.out + (size_t)g * a.stride;
     if (st) {
@@ -357,27 +374,21 @@ __global__ void __launch_bounds__(32 * kPrepWarpGenomes) prepare_warp_kernel(con
     const GeneLayout L = gene_layout((uint32_t)n, (uint32_t)m);
     uint32_t *okey = reinterpret_cast<uint32_t *>(rec + L.nkey);
     uint4 *oattr = reinterpret_cast<uint4 *>(rec + L.nattr);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int e = (r << 5) | lane;
-        if (e < n) {
-            const float *row = nd + (size_t)(vn[r] & 63u) * 5;
-            okey[e] = vn[r] >> 6;
-            oattr[e] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
-                                  __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
-        }
+    for (int e = lane; e < n; e += 32) {
+        const uint32_t v = (uint32_t)nk[e];
+        const float *row = nd + (size_t)(v & 63u) * 5;
+        okey[e] = v >> 6;
+        oattr[e] = make_uint4(__float_as_uint(__ldg(row + 1)), __float_as_uint(__ldg(row + 2)),
+                              __float_as_uint(__ldg(row + 3)), __float_as_uint(__ldg(row + 4)));
     }
     for (int j = n + lane; j < (int)((L.nattr - L.nkey) / 4); j += 32) okey[j] = 0xffffffffu;   // pad
     unsigned long long *ockey = reinterpret_cast<unsigned long long *>(rec + L.ckey);
     float2 *ocattr = reinterpret_cast<float2 *>(rec + L.cattr);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int e = (r << 5) | lane;
-        if (e < m) {
-            const float4 row = __ldg(cn + (vc[r] & 0x1fffu));
-            ockey[e] = vc[r] >> 13;
-            ocattr[e] = make_float2(row.w, row.z != 0.0f ? 1.0f : 0.0f);
-        }
+    for (int e = lane; e < m; e += 32) {
+        const unsigned long long v = ck[e];
+        const float4 row = __ldg(cn + (v & 0x1fffu));
+        ockey[e] = v >> 13;
+        ocattr[e] = make_float2(row.w, row.z != 0.0f ? 1.0f : 0.0f);
     }
     if (lane == 0) {
         *reinterpret_cast<uint4 *>(rec) = make_uint4((uint32_t)n, (uint32_t)m, 0u, L.used);
