@@ -25,7 +25,8 @@
  *
  * Genome encoding (Section 3.1)
  *   nodes_dev f32 [pop][max_nodes][5]: (key, bias, response, aggregation, activation)
- *   conns_dev f32 [pop][max_conns][4]: (in key, out key, enabled, weight)
+ *   conns_dev f32 [pop][max_conns][4]: (in key, out key, enabled, weight);
+ *     with max_conns = 0 it holds nothing and may be NULL
  *   A node row is present when its key is not NaN; a connection row when its
  *   in key, out key and enabled flag are not NaN.  Absent (NaN) rows may sit
  *   anywhere, also between present rows (node or connection removal writes

@@ -917,7 +917,8 @@ extern "C" int neat_distance_prepare(const float *nodes_dev, const float *conns_
     if (!dims_ok(d)) return invalid("neat_distance_prepare: invalid dims");
     if (pop < 0) return invalid("neat_distance_prepare: pop < 0");
     if (pop == 0) return NEAT_OK;
-    if (!nodes_dev || !conns_dev || !genes_dev) return invalid("neat_distance_prepare: null pointer");
+    if (!nodes_dev || (!conns_dev && d.max_conns > 0) || !genes_dev)
+        return invalid("neat_distance_prepare: null pointer");
     if ((reinterpret_cast<uintptr_t>(conns_dev) & 15u) || (reinterpret_cast<uintptr_t>(genes_dev) & 15u))
         return invalid("neat_distance_prepare: conns and genes must be 16-byte aligned");
     PrepArgs a;

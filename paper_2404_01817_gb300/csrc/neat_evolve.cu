@@ -420,7 +420,7 @@ extern "C" int neat_mutate(float *nodes_dev, float *conns_dev, int32_t pop, neat
     if (!dims_ok(d) || !m) return invalid("neat_mutate: invalid dims or config");
     if (pop < 0) return invalid("neat_mutate: pop < 0");
     if (pop == 0) return NEAT_OK;
-    if (!nodes_dev || !conns_dev || !words_dev || !normals_dev || !new_keys_dev)
+    if (!nodes_dev || (!conns_dev && d.max_conns > 0) || !words_dev || !normals_dev || !new_keys_dev)
         return invalid("neat_mutate: null pointer");
     if (reinterpret_cast<uintptr_t>(conns_dev) & 15u) return invalid("neat_mutate: conns must be 16-byte aligned");
     if (m->n_activation_options < 0 || m->n_activation_options > 8 || m->n_aggregation_options < 0 ||
@@ -491,7 +491,8 @@ extern "C" int neat_crossover(const float *nodes_dev, const float *conns_dev, in
     if (!dims_ok(d)) return invalid("neat_crossover: invalid dims");
     if (pop < 0 || n_children < 0) return invalid("neat_crossover: sizes must be >= 0");
     if (n_children == 0) return NEAT_OK;
-    if (!nodes_dev || !conns_dev || !parents_dev || !words_dev || !nodes_out_dev || !conns_out_dev)
+    if (!nodes_dev || (!conns_dev && d.max_conns > 0) || !parents_dev || !words_dev || !nodes_out_dev ||
+        (!conns_out_dev && d.max_conns > 0))
         return invalid("neat_crossover: null pointer");
     if ((reinterpret_cast<uintptr_t>(conns_dev) & 15u) || (reinterpret_cast<uintptr_t>(conns_out_dev) & 15u))
         return invalid("neat_crossover: connection tensors must be 16-byte aligned");

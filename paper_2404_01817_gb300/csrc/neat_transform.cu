@@ -334,7 +334,8 @@ static int transform_impl(const float *nodes_dev, const float *conns_dev, int32_
     if (!dims_ok(d)) return invalid("neat_transform: invalid dims");
     if (pop < 0) return invalid("neat_transform: pop < 0");
     if (pop == 0) return NEAT_OK;
-    if (!nodes_dev || !conns_dev || !transformed_dev) return invalid("neat_transform: null pointer");
+    if (!nodes_dev || (!conns_dev && d.max_conns > 0) || !transformed_dev)
+        return invalid("neat_transform: null pointer");
     if ((reinterpret_cast<uintptr_t>(conns_dev) & 15u) || (reinterpret_cast<uintptr_t>(transformed_dev) & 15u))
         return invalid("neat_transform: conns and transformed must be 16-byte aligned");
     const size_t stride = record_stride(d);

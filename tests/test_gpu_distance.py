@@ -226,6 +226,26 @@ def test_invalid_and_empty_genomes(neat):
     assert out[4, 4] == 0.0 and out[0, 4] == 3.0
 
 
+def test_genomes_without_connection_rows(neat):
+    """max_conns = 0: genes are nodes only, and the connection term is 0;
+    the same genomes with 8 all-NaN connection rows and with 100 node rows
+    give the same bits."""
+    p = _related(14, 60)
+    nodes = p.nodes
+    ref, _, _ = oracle.distance(nodes, np.zeros((60, 0, 4), np.float32), nodes[:11],
+                                np.zeros((11, 0, 4), np.float32), 1.0, 0.5)
+    outs = []
+    for nmax, cmax in ((24, 0), (24, 8), (100, 0)):
+        nd = _pad(nodes, nmax)
+        cn = np.full((60, cmax, 4), np.nan, np.float32)
+        d, genes, st = _prepare(neat, nd, cn)
+        assert (st == 0).all()
+        outs.append(neat.neat_distance(genes, 60, genes, 11, d, 1.0, 0.5).cpu().numpy())
+    assert_outputs_close(outs[0], ref, what="nodes only")
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
 def test_speciate_matches_oracle(neat):
     import torch
     p = _related(7, 500)

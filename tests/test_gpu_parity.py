@@ -233,6 +233,13 @@ def test_forward_edge_cases(neat):
     d0, rec0 = _check_transform(neat, pop0, "no inputs")
     y = neat.neat_forward(rec0, 1, d0, torch.empty((1, 3, 0), device="cuda")).cpu().numpy()
     assert_outputs_close(y, oracle.forward(pop0.nodes, pop0.conns, 0, 2, np.zeros((1, 3, 0), np.float32)))
+    # max_conns = 0: no connection rows at all (the empty tensor's pointer is NULL)
+    ant = W.ant_population(3, 20)
+    popc = W.Population(ant.nodes, np.zeros((20, 0, 4), np.float32), 27, 8)
+    dc, recc = _check_transform(neat, popc, "no connection rows")
+    x = W.normal_inputs(4, (20, 2, 27))
+    y = neat.neat_forward(recc, 20, dc, _dev(x)).cpu().numpy()
+    assert_outputs_close(y, oracle.forward(popc.nodes, popc.conns, 27, 8, x))
 
 
 def test_steps_graph_matches_per_step_forward(neat):
