@@ -55,10 +55,14 @@ __device__ __forceinline__ int choose(uint32_t u, int k)
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
 // Block-wide rank selection: rows [0, R) in order, `pred(row)` the
-// candidates; returns (via shared memory) the row of rank `rank` among them
-// (-1 if there are not that many) and the candidate count.
-template <typename Pred>
-__device__ int select_rank(int R, Pred pred, int rank, int *s_cnt, int *s_row, int *total_out)
+// candidates.  One block scan counts them; then, with the count known to
+// every thread, the rows of ranks rank_of(total) (and rank2_of(total), when
+// asked for) among the candidates are found (-1 where there are not that
+// many).  Returns the first row, the second through *row2, the count
+// through *total_out.
+template <typename Pred, typename RankOf, typename Rank2Of>
+__device__ int select_ranks(int R, Pred pred, RankOf rank_of, Rank2Of rank2_of, int *s_cnt, int *s_row,
+                            int *total_out, int *row2)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int chunk = (R + nt - 1) / nt;
@@ -74,7 +78,7 @@ __device__ int select_rank(int R, Pred pred, int rank, int *s_cnt, int *s_row, i
         if (lane >= o) incl += v;
     }
     if (lane == 31) s_cnt[warp] = incl;
-    if (tid == 0) *s_row = -1;
+    if (tid == 0) s_row[0] = s_row[1] = -1;
     __syncthreads();
     int base = 0, total = 0;
     for (int w = 0; w < nt / 32; ++w) {
@@ -82,19 +86,41 @@ __device__ int select_rank(int R, Pred pred, int rank, int *s_cnt, int *s_row, i
         total += s_cnt[w];
     }
     const int excl = base + incl - c;
-    if (rank >= excl && rank < excl + c) {
-        int k = rank - excl;
-        for (int r = r0; r < r1; ++r)
-            if (pred(r) && k-- == 0) {
-                *s_row = r;
-                break;
-            }
-    }
+    auto find = [&](int rank, int *out) {
+        if (rank >= 0 && rank >= excl && rank < excl + c) {
+            int k = rank - excl;
+            for (int r = r0; r < r1; ++r)
+                if (pred(r) && k-- == 0) {
+                    *out = r;
+                    break;
+                }
+        }
+    };
+    find(rank_of(total), s_row);
+    find(rank2_of(total), s_row + 1);
     __syncthreads();
-    const int row = *s_row;
+    const int row = s_row[0];
+    if (row2) *row2 = s_row[1];
     *total_out = total;
     __syncthreads();
     return row;
+}
+
+// The candidate of rank `rank` (-1 if there are not that many).
+template <typename Pred>
+__device__ int select_rank(int R, Pred pred, int rank, int *s_cnt, int *s_row, int *total_out)
+{
+    return select_ranks(
+        R, pred, [=](int) { return rank; }, [](int) { return -1; }, s_cnt, s_row, total_out, nullptr);
+}
+
+// The candidate chosen by the random word u among all of them (-1 if none).
+template <typename Pred>
+__device__ int select_choose(int R, Pred pred, uint32_t u, int *s_cnt, int *s_row, int *total_out)
+{
+    return select_ranks(
+        R, pred, [=](int total) { return total > 0 ? choose(u, total) : -1; }, [](int) { return -1; }, s_cnt,
+        s_row, total_out, nullptr);
 }
 
 __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
@@ -108,7 +134,7 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
     short *inr = reinterpret_cast<short *>(ce + a.C);                        // [C] rows of the endpoints
     short *outr = inr + a.C;
     unsigned char *seen = reinterpret_cast<unsigned char *>(outr + a.C);     // [N]
-    __shared__ int s_cnt[kEvoThreads / 32], s_row;
+    __shared__ int s_cnt[kEvoThreads / 32], s_row[2];
     const int g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int N = a.N, C = a.C;
     float *nodes = a.nodes + (size_t)g * N * 5;
@@ -134,12 +160,11 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
     if (below(u[0], a.t_node_add)) {
         const float nkey = (float)__ldg(a.new_keys + g);
         auto enabled = [&](int c) { return conn_present(c) && ce[c] != 0.0f; };
-        select_rank(C, enabled, 0, s_cnt, &s_row, &total);
-        const int k = total;
-        const int pick = k > 0 ? select_rank(C, enabled, choose(u[1], k), s_cnt, &s_row, &total) : -1;
-        const int rn = select_rank(N, node_free, 0, s_cnt, &s_row, &total);
-        const int ra = select_rank(C, conn_free, 0, s_cnt, &s_row, &total);
-        const int rb = select_rank(C, conn_free, 1, s_cnt, &s_row, &total);
+        const int pick = select_choose(C, enabled, u[1], s_cnt, s_row, &total);
+        const int rn = select_rank(N, node_free, 0, s_cnt, s_row, &total);
+        int rb = -1;
+        const int ra = select_ranks(
+            C, conn_free, [](int) { return 0; }, [](int) { return 1; }, s_cnt, s_row, &total, &rb);
         bool used = false;
         for (int r = tid; r < N; r += nt) used |= node_present(r) && nk[r] == nkey;
         used = __syncthreads_or(used);
@@ -168,9 +193,8 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
     if (below(u[2], a.t_node_delete)) {
         const float io_end = (float)(a.I + a.O);
         auto hidden = [&](int r) { return node_present(r) && nk[r] >= io_end; };
-        select_rank(N, hidden, 0, s_cnt, &s_row, &total);
+        const int rd = select_choose(N, hidden, u[3], s_cnt, s_row, &total);
         if (total > 0) {
-            const int rd = select_rank(N, hidden, choose(u[3], total), s_cnt, &s_row, &total);
             const float q = nk[rd];
             for (int c = tid; c < C; c += nt)
                 if (conn_present(c) && (ci[c] == q || co[c] == q)) {
@@ -191,14 +215,12 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
         const float in_end = (float)a.I;
         auto target = [&](int r) { return node_present(r) && nk[r] >= in_end; };
         int ks = 0, kt = 0;
-        select_rank(N, node_present, 0, s_cnt, &s_row, &ks);
-        select_rank(N, target, 0, s_cnt, &s_row, &kt);
+        const int rs = select_choose(N, node_present, u[5], s_cnt, s_row, &ks);
+        const int rt = select_choose(N, target, u[6], s_cnt, s_row, &kt);
         if (ks > 0 && kt > 0) {
-            const int rs = select_rank(N, node_present, choose(u[5], ks), s_cnt, &s_row, &total);
-            const int rt = select_rank(N, target, choose(u[6], kt), s_cnt, &s_row, &total);
             const float s = nk[rs], t = nk[rt];
             const int existing =
-                select_rank(C, [&](int c) { return conn_present(c) && ci[c] == s && co[c] == t; }, 0, s_cnt, &s_row,
+                select_rank(C, [&](int c) { return conn_present(c) && ci[c] == s && co[c] == t; }, 0, s_cnt, s_row,
                             &total);
             if (existing >= 0) {
                 if (tid == 0) {
@@ -253,7 +275,7 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
                     }
                 }
                 if (!reject) {
-                    const int rf = select_rank(C, conn_free, 0, s_cnt, &s_row, &total);
+                    const int rf = select_rank(C, conn_free, 0, s_cnt, s_row, &total);
                     if (rf >= 0 && tid == 0) {
                         const float w = fmaf(a.w_std, z[0], a.w_mean);
                         *reinterpret_cast<float4 *>(conns + (size_t)rf * 4) = make_float4(s, t, 1.0f, w);
@@ -267,9 +289,8 @@ __global__ void __launch_bounds__(kEvoThreads) mutate_kernel(const MutArgs a)
 
     // 4. connection deletion
     if (below(u[7], a.t_conn_delete)) {
-        select_rank(C, conn_present, 0, s_cnt, &s_row, &total);
+        const int rc = select_choose(C, conn_present, u[8], s_cnt, s_row, &total);
         if (total > 0) {
-            const int rc = select_rank(C, conn_present, choose(u[8], total), s_cnt, &s_row, &total);
             if (tid == 0) {
                 *reinterpret_cast<float4 *>(conns + (size_t)rc * 4) = make_float4(qnan(), qnan(), qnan(), qnan());
                 ci[rc] = co[rc] = ce[rc] = qnan();
