@@ -1339,6 +1339,22 @@ def main():
     h2d = nodes_h.numel() * 4 + conns_h.numel() * 4 + obs_h.numel() * 4
     d2h = act_h.numel() * 4
 
+    # the host link on this machine, now: one episode's uploads and its downloads,
+    # each direction timed alone (best of 3); the two overlap in the episodes,
+    # so the slower one sets the end-to-end floor
+    def copy_s(pairs, st):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        with torch.cuda.stream(st):
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+        b.record(st)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+    t_up = min(copy_s([(nodes, nodes_h), (conns, conns_h), (obs, obs_h)], up_stream) for _ in range(3))
+    t_dn = min(copy_s([(act_h, act)], down_stream) for _ in range(3))
+    link_floor = world * POP * S / max(t_up, t_dn)
+
     # ---- roofline of the forward kernel: algorithmic bytes per launch
     alg_bytes, n_nodes, n_edges = genome_forward_bytes(pop)
     hdr = rec.view(POP, -1)[:, :32].cpu().numpy().view(np.uint32)
@@ -1406,8 +1422,12 @@ def main():
                 "form": f"pinned host genomes and observations in, actions out, every episode (transform, lane "
                         f"compile, forwards); {CH} chunks (the first {bounds[1]} steps, then up to 100): uploads run "
                         "ahead of the graphs on their own copy stream, across episodes (a chunk's waits for the "
-                        "previous episode's forward of it), downloads behind on another; copy-bound (about 210 GB/s "
-                        "host to device, 190 back, measured alone)"},
+                        "previous episode's forward of it), downloads behind on another; copy-bound: see link",
+                "link": {"h2d_gbs": h2d / t_up / 1e9, "d2h_gbs": d2h / t_dn / 1e9, "floor": link_floor,
+                         "frac_of_floor": world * POP * S * n_e2e / t_e2e / link_floor,
+                         "note": "one episode's uploads and downloads, each direction timed alone on this box right "
+                                 "after the e2e episodes (best of 3); floor = genome-forwards per episode over the "
+                                 "slower direction's time"}},
         "fused_multistep": {"value": world * POP * S * n_fused / t_fused, "unit": UNIT, "episodes": n_fused,
                             "us_per_step": t_fused / n_fused / S * 1e6,
                             "form": "one launch per episode (neat_forward_fused, level-walk kernel), records read "
