@@ -38,14 +38,26 @@ def test_genome_forward_bytes_of_the_ant_population_scale():
     assert 16.0e6 < alg < 16.6e6
 
 
-def test_issue_roofline_needs_matching_sources():
-    """A recorded count is used only while its kernel's sources hash the same;
-    the fraction is instructions / time / (4 schedulers x SMs x clock)."""
-    files = ("neat_distance.cu", "neat_device.cuh", "neat_internal.h")
+def test_issue_roofline_needs_matching_sources(tmp_path, monkeypatch):
+    """A recorded count is used only while its kernel's sources hash the
+    same (any byte changed: no roofline); the fraction is instructions /
+    time / (4 schedulers x SMs x clock).  Checked on a scratch tree."""
+    import json
+    csrc = tmp_path / "paper_2404_01817_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_text("kernel one")
+    (csrc / "k.cuh").write_text("helpers")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    files = ("k.cu", "k.cuh")
     assert bench.source_hash(files) == bench.source_hash(files)
-    assert bench.source_hash(files) != bench.source_hash(files[:2])
-    r = bench.issue_roofline_from_profile("distance_traffic.json", files, 1e-4, 152, 2070.0)
-    assert r is not None and r["bound"] == "issue"
-    assert abs(r["frac"] - r["instructions_per_launch"] / 1e-4 / (4 * 152 * 2070.0e6)) < 1e-12
-    assert bench.issue_roofline_from_profile("distance_traffic.json", files[:2], 1e-4, 152, 2070.0) is None
-    assert bench.issue_roofline_from_profile("no_such_record.json", files, 1e-4, 152, 2070.0) is None
+    assert bench.source_hash(files) != bench.source_hash(files[:1])
+    rec = {"kernel_hash": bench.source_hash(files), "warp_instructions_per_launch": 5.0e7}
+    (tmp_path / "profiles" / "k.json").write_text(json.dumps(rec))
+    r = bench.issue_roofline_from_profile("k.json", files, 1e-4, 152, 2070.0)
+    assert r is not None and r["bound"] == "issue" and r["instructions_per_launch"] == 5.0e7
+    assert abs(r["frac"] - 5.0e7 / 1e-4 / (4 * 152 * 2070.0e6)) < 1e-12
+    assert bench.issue_roofline_from_profile("k.json", files[:1], 1e-4, 152, 2070.0) is None
+    assert bench.issue_roofline_from_profile("missing.json", files, 1e-4, 152, 2070.0) is None
+    (csrc / "k.cu").write_text("kernel two")                 # the kernel changed since the count was taken
+    assert bench.issue_roofline_from_profile("k.json", files, 1e-4, 152, 2070.0) is None
