@@ -191,6 +191,13 @@ def test_lanes_edge_cases(neat):
     d0, rec0, lanes0 = _prepare(neat, pop0)
     y0 = neat.neat_forward_lanes(lanes0, 1, d0, torch.empty((1, 0), device="cuda")).cpu().numpy()
     assert_outputs_close(y0, oracle.forward(pop0.nodes, pop0.conns, 0, 2, np.zeros((1, 1, 0), np.float32))[:, 0])
+    # no connection rows at all (max_conns = 0, the empty tensor's pointer is NULL)
+    ant = W.ant_population(3, 40)
+    popc = W.Population(ant.nodes, np.zeros((40, 0, 4), np.float32), 27, 8)
+    dc, recc, lanesc = _prepare(neat, popc)
+    xc = W.normal_inputs(4, (40, 27))
+    yc = neat.neat_forward_lanes(lanesc, 40, dc, _dev(xc)).cpu().numpy()
+    assert_outputs_close(yc, oracle.forward(popc.nodes, popc.conns, 27, 8, xc[:, None, :])[:, 0])
     # an empty population packs and runs
     dz = neat.dims(27, 8, 50, 200)
     lz = torch.empty(max(neat.neat_lanes_bytes(0, dz), 256), dtype=torch.uint8, device="cuda")
